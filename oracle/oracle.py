@@ -1,0 +1,222 @@
+"""FP64 CPU oracle for FCC TDoA estimation -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference leg may import this module.  The product package never imports it and
+shares no code with it.
+
+This is a thin numpy/ctypes shell over ``fcc_oracle.c`` (compiled on first use
+with the system C compiler).  Every numeric step lives in the C file, which
+follows the paper's definitions literally in FP64:
+
+* Sec. 3 -- candidate grid tau_i = -L + i/r  (I = 2rL + 1).
+* Eq. 3 -- W(i, f) = exp(j 2 pi f tau_i / N), f = 0..N/2.
+* Sec. 4 -- W = U S V^H by the C file's own complex Jacobi SVD, truncated to
+  rank K (W_K); K from the energy rule when not given.
+* Sec. 2 (eq. 1, alpha = 1) -- R_hat = X_i X_j^* / |X_i X_j^*|.
+* Eq. 2 / Eq. 4 -- y = 2 Re{W_K x}; argmax; three-point quadratic refinement.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fcc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle_fcc.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def build(force: bool = False) -> str:
+    """Compile fcc_oracle.c into liboracle_fcc.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.or_grid.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+            lib.or_grid.restype = ctypes.c_int
+            lib.or_build_W.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+            lib.or_build_W.restype = None
+            lib.or_svd.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   ctypes.c_int]
+            lib.or_svd.restype = ctypes.c_int
+            lib.or_rank_energy.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            lib.or_rank_energy.restype = ctypes.c_int
+            lib.or_lowrank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp,
+                                       _dp, _dp, _dp, _dp, _dp, _dp]
+            lib.or_lowrank.restype = None
+            lib.or_phat.argtypes = [_fp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+            lib.or_phat.restype = None
+            lib.or_correlate.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.or_correlate.restype = None
+            lib.or_argmax.argtypes = [_dp, ctypes.c_int]
+            lib.or_argmax.restype = ctypes.c_int
+            lib.or_parabola.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double]
+            lib.or_parabola.restype = ctypes.c_double
+            lib.or_tdoa.argtypes = [_fp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _ip, _dp, _dp,
+                                    _dp, ctypes.c_int]
+            lib.or_tdoa.restype = None
+            lib.or_max_threads.argtypes = []
+            lib.or_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def max_threads() -> int:
+    return int(_load().or_max_threads())
+
+
+def grid(L: int, den: int) -> np.ndarray:
+    """Sec. 3: the candidate grid tau_i = -L + i/den (I = 2*L*den + 1)."""
+    lib = _load()
+    I = lib.or_grid(L, den, None)
+    taus = np.empty(I, np.float64)
+    lib.or_grid(L, den, _d(taus))
+    return taus
+
+
+def build_W(N: int, taus: np.ndarray) -> np.ndarray:
+    """Eq. 3: W(i, f) = exp(j 2 pi f tau_i / N), shape [I, N/2+1], complex128."""
+    taus = np.ascontiguousarray(taus, np.float64)
+    I, B = len(taus), N // 2 + 1
+    wr = np.empty((I, B), np.float64)
+    wi = np.empty((I, B), np.float64)
+    _load().or_build_W(N, I, _d(taus), _d(wr), _d(wi))
+    return wr + 1j * wi
+
+
+def svd(A: np.ndarray, max_sweeps: int = 80):
+    """Sec. 4: A = U diag(s) V^H by the oracle's own complex Jacobi SVD.
+
+    Returns (U [m, r], s [r] descending, V [n, r]) with r = min(m, n).
+    """
+    A = np.asarray(A, np.complex128)
+    m, n = A.shape
+    r = min(m, n)
+    ar = np.ascontiguousarray(A.real)
+    ai = np.ascontiguousarray(A.imag)
+    s = np.empty(r)
+    ur, ui = np.empty((m, r)), np.empty((m, r))
+    vr, vi = np.empty((n, r)), np.empty((n, r))
+    sweeps = _load().or_svd(m, n, _d(ar), _d(ai), _d(s), _d(ur), _d(ui), _d(vr), _d(vi),
+                            max_sweeps)
+    if sweeps < 0:
+        raise RuntimeError("oracle Jacobi SVD did not converge")
+    return ur + 1j * ui, s, vr + 1j * vi
+
+
+def rank_energy(s: np.ndarray, energy: float = 0.999, tie_rel: float = 1e-12) -> int:
+    """Sec. 4 ("K set experimentally"): smallest K holding `energy` of sum(s^2)."""
+    s = np.ascontiguousarray(s, np.float64)
+    return int(_load().or_rank_energy(_d(s), len(s), energy, tie_rel))
+
+
+def lowrank(U, s, V, K: int) -> np.ndarray:
+    """Sec. 4: W_K = U_K diag(s_K) V_K^H."""
+    m, r = U.shape
+    n = V.shape[0]
+    ur, ui = np.ascontiguousarray(U.real), np.ascontiguousarray(U.imag)
+    vr, vi = np.ascontiguousarray(V.real), np.ascontiguousarray(V.imag)
+    s = np.ascontiguousarray(s, np.float64)
+    wr, wi = np.empty((m, n)), np.empty((m, n))
+    _load().or_lowrank(m, n, r, K, _d(s), _d(ur), _d(ui), _d(vr), _d(vi), _d(wr), _d(wi))
+    return wr + 1j * wi
+
+
+def phat(X_frame: np.ndarray, i: int, j: int) -> np.ndarray:
+    """Sec. 2: R_hat = X_i X_j^* / |X_i X_j^*| for one frame X[m, f] (complex64)."""
+    X = np.ascontiguousarray(X_frame, np.complex64)
+    B = X.shape[1]
+    xr, xi = np.empty(B), np.empty(B)
+    _load().or_phat(X.ctypes.data_as(_fp), B, i, j, _d(xr), _d(xi))
+    return xr + 1j * xi
+
+
+def correlate(W: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Eq. 4: y = 2 Re{W x}."""
+    I, B = W.shape
+    wr, wi = np.ascontiguousarray(W.real), np.ascontiguousarray(W.imag)
+    xr, xi = np.ascontiguousarray(np.real(x), np.float64), np.ascontiguousarray(np.imag(x), np.float64)
+    y = np.empty(I)
+    _load().or_correlate(I, B, _d(wr), _d(wi), _d(xr), _d(xi), _d(y))
+    return y
+
+
+def argmax(y: np.ndarray) -> int:
+    y = np.ascontiguousarray(y, np.float64)
+    return int(_load().or_argmax(_d(y), len(y)))
+
+
+def parabola(y: np.ndarray, idx: int, tau_idx: float, delta: float) -> float:
+    y = np.ascontiguousarray(y, np.float64)
+    return float(_load().or_parabola(_d(y), len(y), idx, tau_idx, delta))
+
+
+class Basis:
+    """The oracle's rank-K operator for one (N, lag grid) key.
+
+    W (Eq. 3) -> complex Jacobi SVD (Sec. 4) -> K by the energy rule unless
+    given -> W_K.  `full` keeps W itself (the eq. 2 / GCC-PHAT operator).
+    """
+
+    def __init__(self, N: int, L: int, den: int, K: int | None = None, energy: float = 0.999):
+        self.N, self.L, self.den = N, L, den
+        self.B = N // 2 + 1
+        self.taus = grid(L, den)
+        self.I = len(self.taus)
+        self.delta = 1.0 / den
+        self.W = build_W(N, self.taus)
+        self.U, self.s, self.V = svd(self.W)
+        self.K = rank_energy(self.s, energy) if K is None else int(K)
+        self.WK = lowrank(self.U, self.s, self.V, self.K)
+
+
+def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: bool = False,
+         threads: int | None = None):
+    """The per-pair-frame pipeline over spectra X[T, M, N/2+1] (complex64).
+
+    For every frame and every pair i < j (lexicographic): R_hat (Sec. 2),
+    y = 2 Re{W x} (Eq. 4), argmax (lowest index on ties), quadratic refinement.
+    Returns (idx [T, P] int32, peak [T, P] f64, tau_hat [T, P] f64, y [T, P, I] or None).
+    """
+    X = np.ascontiguousarray(X, np.complex64)
+    T, M, B = X.shape
+    N = 2 * (B - 1)
+    I = W.shape[0]
+    assert W.shape[1] == B and len(taus) == I
+    P = M * (M - 1) // 2
+    wr, wi = np.ascontiguousarray(W.real), np.ascontiguousarray(W.imag)
+    taus = np.ascontiguousarray(taus, np.float64)
+    idx = np.empty((T, P), np.int32)
+    peak = np.empty((T, P))
+    tau = np.empty((T, P))
+    y = np.empty((T, P, I)) if want_y else None
+    nt = max_threads() if threads is None else int(threads)
+    _load().or_tdoa(X.ctypes.data_as(_fp), T, M, N, I, _d(wr), _d(wi), _d(taus), float(delta),
+                    idx.ctypes.data_as(_ip), _d(peak), _d(tau),
+                    _d(y) if want_y else None, nt)
+    return idx, peak, tau, y

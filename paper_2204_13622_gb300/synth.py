@@ -1,0 +1,202 @@
+"""Seeded synthetic microphone-array spectra.
+
+This module only makes inputs: array geometries, far-field sources with
+fractional delays, additive noise and an STFT front-end.  It contains none of
+the FCC method's arithmetic (no phase transform, no correlation, no bases), so
+that both the CUDA path and the FP64 oracle can be fed the same bytes.
+
+Two generators:
+
+* :func:`time_domain_spectra` -- the front-end of Sec. 2 done literally: a time
+  signal per microphone (white Gaussian source, fractional delays applied as a
+  phase ramp on a zero-padded FFT of the whole signal, white noise at a given
+  SNR), then a periodic-Hann STFT with frame N and hop N/2 (50 % overlap).
+* :func:`stft_domain_spectra` -- for large frame counts: sources drawn directly
+  in the STFT domain (complex Gaussian shaped to a pink 1/f power spectrum,
+  random on/off envelopes of 20-200 ms), each delayed per microphone by the
+  exact phase ramp exp(-j 2 pi f delay / N), plus white noise at a per-segment
+  SNR.  Runs on any torch device, chunked, so 17 GB tensors can be made on
+  the GPU.
+
+Delay convention: a microphone at position r hears a far-field source in unit
+direction u at time offset delay = -fs (r . u) / c samples (closer = earlier).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SPEED_OF_SOUND = 343.0
+
+
+# ----------------------------------------------------------------------------
+# geometries
+# ----------------------------------------------------------------------------
+def square_array(side: float) -> np.ndarray:
+    """Four mics on the corners of a square of the given side (metres)."""
+    a = side / 2.0
+    return np.array([[a, a, 0.0], [-a, a, 0.0], [-a, -a, 0.0], [a, -a, 0.0]])
+
+
+def circular_array(n_mics: int, radius: float) -> np.ndarray:
+    """Uniform circular array, mic m at angle 2 pi m / n_mics."""
+    ang = 2.0 * np.pi * np.arange(n_mics) / n_mics
+    return np.stack([radius * np.cos(ang), radius * np.sin(ang), np.zeros(n_mics)], axis=1)
+
+
+def grid_array(nx: int, ny: int, pitch: float) -> np.ndarray:
+    """nx x ny planar grid with the given pitch, centred on the origin."""
+    xs = (np.arange(nx) - (nx - 1) / 2.0) * pitch
+    ys = (np.arange(ny) - (ny - 1) / 2.0) * pitch
+    return np.array([[x, y, 0.0] for y in ys for x in xs])
+
+
+def max_distance(xyz: np.ndarray) -> float:
+    d = xyz[:, None, :] - xyz[None, :, :]
+    return float(np.sqrt((d ** 2).sum(-1)).max())
+
+
+def lag_extent(xyz: np.ndarray, fs: float, c: float = SPEED_OF_SOUND) -> int:
+    """L = ceil(d_max fs / c): the integer lag half-range that holds every pair."""
+    return int(math.ceil(max_distance(xyz) * fs / c - 1e-9))
+
+
+def unit_vector(azimuth: float, elevation: float = 0.0) -> np.ndarray:
+    return np.array([math.cos(elevation) * math.cos(azimuth),
+                     math.cos(elevation) * math.sin(azimuth), math.sin(elevation)])
+
+
+def far_field_delays(xyz: np.ndarray, direction: np.ndarray, fs: float,
+                     c: float = SPEED_OF_SOUND) -> np.ndarray:
+    """Per-mic delay (samples) of a far-field source from `direction`."""
+    return -fs * (xyz @ direction) / c
+
+
+# ----------------------------------------------------------------------------
+# time-domain path (small inputs)
+# ----------------------------------------------------------------------------
+def stft(x: np.ndarray, N: int, hop: int) -> np.ndarray:
+    """Periodic-Hann STFT without centre padding: [n_ch, L] -> [T, n_ch, N/2+1]."""
+    n_ch, L = x.shape
+    T = 1 + (L - N) // hop
+    win = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(N) / N)
+    idx = np.arange(T)[:, None] * hop + np.arange(N)[None, :]
+    frames = x[:, idx] * win  # [n_ch, T, N]
+    return np.fft.rfft(frames, axis=-1).transpose(1, 0, 2)
+
+
+@dataclass
+class Recording:
+    spectra: np.ndarray  # complex64 [T, M, N/2+1]
+    xyz: np.ndarray
+    fs: float
+    N: int
+    hop: int
+    delays: np.ndarray  # per-mic delays of the (first) source, samples
+    meta: dict = field(default_factory=dict)
+
+
+def time_domain_spectra(xyz: np.ndarray, fs: float, N: int, hop: int, n_samples: int,
+                        seed: int, snr_db: float = 20.0, azimuth: float | None = None,
+                        elevation: float = 0.0, c: float = SPEED_OF_SOUND) -> Recording:
+    """One far-field white-Gaussian source plus white noise, then the STFT."""
+    rng = np.random.default_rng(seed)
+    if azimuth is None:
+        azimuth = float(rng.uniform(0.0, 2.0 * np.pi))
+    delays = far_field_delays(xyz, unit_vector(azimuth, elevation), fs, c)
+    src = rng.standard_normal(n_samples)
+    nfft = 1 << int(math.ceil(math.log2(2 * n_samples)))
+    S = np.fft.rfft(src, nfft)
+    k = np.arange(nfft // 2 + 1)
+    sig = np.stack([np.fft.irfft(S * np.exp(-2j * np.pi * k * d / nfft), nfft)[:n_samples]
+                    for d in delays])
+    noise = rng.standard_normal(sig.shape) * (sig.std() * 10.0 ** (-snr_db / 20.0))
+    X = stft(sig + noise, N, hop).astype(np.complex64)
+    return Recording(X, xyz, fs, N, hop, delays, dict(azimuth=azimuth, snr_db=snr_db))
+
+
+def config_small_square(seed: int = 1) -> Recording:
+    """4-mic square (4.5 cm side), fs 16 kHz, N 512 / hop 256, 1 s, 20 dB SNR."""
+    return time_domain_spectra(square_array(0.045), 16000.0, 512, 256, 16000, seed, 20.0)
+
+
+# ----------------------------------------------------------------------------
+# STFT-domain path (large inputs, any torch device)
+# ----------------------------------------------------------------------------
+def stft_domain_spectra(T: int, xyz: np.ndarray, fs: float, N: int, hop: int, seed: int,
+                        device="cpu", out=None, max_sources: int = 3,
+                        snr_db: tuple = (0.0, 30.0), segment_s: float = 1.0,
+                        onoff_ms: tuple = (20.0, 200.0), chunk: int | None = None,
+                        c: float = SPEED_OF_SOUND):
+    """Spectra [T, M, N/2+1] complex64 made directly in the STFT domain.
+
+    Per 1-s segment: 1..max_sources sources with uniform azimuth in [0, 2 pi)
+    and elevation in [0, pi/2], and an SNR uniform in `snr_db`.  Each source is
+    complex Gaussian with a pink (1/f power) spectral shape, gated by on/off
+    runs whose lengths are uniform in `onoff_ms`.  Microphone m sees source s
+    through exp(-j 2 pi f delay_{m,s} / N).  Deterministic for a given seed and
+    device.
+    """
+    import torch
+
+    M = xyz.shape[0]
+    B = N // 2 + 1
+    dev = torch.device(device)
+    rng = np.random.default_rng(seed)
+    frames_per_seg = max(1, int(round(segment_s * fs / hop)))
+    n_seg = (T + frames_per_seg - 1) // frames_per_seg
+    # per-segment scene, drawn on the host (small)
+    n_src = rng.integers(1, max_sources + 1, size=n_seg)
+    az = rng.uniform(0.0, 2.0 * np.pi, size=(n_seg, max_sources))
+    el = rng.uniform(0.0, np.pi / 2.0, size=(n_seg, max_sources))
+    snr = rng.uniform(snr_db[0], snr_db[1], size=n_seg)
+    u = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=-1)
+    delays = -fs * np.einsum("mk,gsk->gsm", xyz, u) / c  # [n_seg, S, M]
+    active = (np.arange(max_sources)[None, :] < n_src[:, None]).astype(np.float32)
+    # on/off envelope per source, in frames
+    frame_ms = 1000.0 * hop / fs
+    env = np.zeros((max_sources, T), np.float32)
+    for s in range(max_sources):
+        pos, on = 0, bool(rng.integers(0, 2))
+        while pos < T:
+            run = max(1, int(round(rng.uniform(*onoff_ms) / frame_ms)))
+            if on:
+                env[s, pos:pos + run] = 1.0
+            pos += run
+            on = not on
+    # guarantee at least one source is on in every frame so no frame is pure noise
+    env[0, env.sum(0) == 0] = 1.0
+
+    delays_t = torch.tensor(delays, dtype=torch.float64, device=dev)
+    active_t = torch.tensor(active, device=dev)
+    noise_amp_t = torch.tensor(10.0 ** (-snr / 20.0), dtype=torch.float32, device=dev)
+    env_t = torch.tensor(env, device=dev)
+    f = torch.arange(B, device=dev, dtype=torch.float64)
+    pink = (1.0 / torch.sqrt(torch.clamp(f, min=1.0))).to(torch.float32)
+    pink = pink / torch.sqrt((pink ** 2).mean())
+    if out is None:
+        out = torch.empty((T, M, B), dtype=torch.complex64, device=dev)
+    if chunk is None:  # keep each float64 temporary near 2^27 elements
+        chunk = max(1, (1 << 27) // (max_sources * M * B))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 7919 + 17)
+    for t0 in range(0, T, chunk):
+        t1 = min(T, t0 + chunk)
+        n = t1 - t0
+        seg = torch.arange(t0, t1, device=dev) // frames_per_seg  # [n]
+        src = torch.randn((max_sources, n, B), dtype=torch.complex64, device=dev, generator=gen)
+        src = src * pink  # [S, n, B]
+        gate = env_t[:, t0:t1] * active_t[seg].T  # [S, n]
+        src = src * gate[:, :, None]
+        # exact phase ramp per (segment, source, mic): exp(-j 2 pi f d / N)
+        d = delays_t[seg]  # [n, S, M]
+        ph = (-2.0 * math.pi / N) * d[..., None] * f  # [n, S, M, B] float64
+        ramp = torch.polar(torch.ones_like(ph, dtype=torch.float32), ph.to(torch.float32))
+        X = torch.einsum("snb,nsmb->nmb", src, ramp)
+        noise = torch.randn((n, M, B), dtype=torch.complex64, device=dev, generator=gen)
+        X = X + noise * noise_amp_t[seg][:, None, None]
+        out[t0:t1] = X
+        del src, ramp, X, noise, ph
+    return out
