@@ -1,0 +1,201 @@
+/*
+ * fcc.h -- C ABI of the GB300 (sm_103a) Fast Cross-Correlation TDoA library.
+ *
+ * Method: Grondin, Maheux, Lauzon, Vincent, Michaud, "Fast Cross-Correlation
+ * for TDoA Estimation on Small Aperture Microphone Arrays".  For every STFT
+ * frame t and every microphone pair (i, j), i < j, the library computes
+ *
+ *   R_hat(f) = X_i(f) X_j(f)^* / |X_i(f) X_j(f)^*|          (Sec. 2, eq. 1, alpha = 1)
+ *   y(tau)   = 2 Re{ W_K x }                                 (Eq. 4 with rank-K W, Sec. 4)
+ *            evaluated through the folded even/odd bases     (Eqs. 6-9)
+ *   tau*     = argmax over the lag grid, plus a quadratic refinement (Sec. 2)
+ *
+ * Conventions used by every entry point:
+ *   - Spectra are complex64 (interleaved float re, im), layout [T][M][B] with
+ *     B = N/2 + 1 bins, C order, frame-major.  Device pointers must be 16-byte
+ *     aligned.
+ *   - Pairs p = 0..P-1, P = M(M-1)/2, enumerate (i, j), i < j, in
+ *     lexicographic order.
+ *   - The lag grid is tau_i = -L + i/den, i = 0..I-1, I = 2 L den + 1 (Sec. 3;
+ *     the paper's "I = 4 ceil(tau_max) + 1" is the den = 2 case).
+ *   - TDoA sign: tau_ij = t_i - t_j in samples, i.e. positive when mic i hears
+ *     the source later than mic j (with R = X_i X_j^* the correlation peaks at
+ *     delta_i - delta_j).
+ *   - Ties in the argmax go to the lowest lag index.
+ *   - The caller owns every input and output buffer.  A plan owns its bases
+ *     and its small device workspace; it is used by one stream at a time.
+ *   - Asynchronous entry points enqueue on the caller's cudaStream_t (passed as
+ *     void*, NULL = legacy default stream) and return without synchronising.
+ *     Argument errors are returned at once; conditions found on the device
+ *     (non-finite input, a bounded wait that expired) are latched in the plan's
+ *     device error word and reported by fcc_plan_sync().
+ *   - No C++ exception crosses this ABI.
+ */
+#ifndef FCC_GB300_H
+#define FCC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FCC_OK = 0,
+    FCC_ERR_INVALID_ARG = 1,   /* a null/misaligned pointer or an out-of-range size */
+    FCC_ERR_UNSUPPORTED = 2,   /* valid request this build does not handle (e.g. M > 16) */
+    FCC_ERR_OOM = 3,           /* a device or pinned-host allocation failed */
+    FCC_ERR_CUDA = 4,          /* a CUDA runtime / cuFFT call failed (see fcc_last_error) */
+    FCC_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+    FCC_ERR_NONFINITE = 6,     /* NaN or Inf in the input spectra (outputs unspecified) */
+    FCC_ERR_NOT_CONVERGED = 7  /* the FP64 Jacobi SVD of the plan did not converge */
+} fcc_status_t;
+
+typedef enum {
+    FCC_PREC_FP32 = 0,  /* FP32 throughout (CUDA-core FFMA path) */
+    FCC_PREC_BF16 = 1,  /* projection operands in BF16, FP32 accumulation (tensor cores) */
+    FCC_PREC_FP16 = 2   /* projection operands in FP16, FP32 accumulation (tensor cores) */
+} fcc_prec_t;
+
+/*
+ * Plan description (Sec. 3 grid, Sec. 4 rank).  All fields are copied.
+ *   n_mics   M, 2 <= M <= 16.
+ *   mic_xyz  host [M][3] positions in metres; read only when tau_max <= 0,
+ *            to derive L = ceil(max pair distance * fs / c).
+ *   fs       sample rate in Hz (> 0).
+ *   N        frame size, a power of two, 16 <= N <= 4096.
+ *   c        speed of sound in m/s; <= 0 selects 343.
+ *   tau_max  lag half-range in samples; L = ceil(tau_max); <= 0: from geometry.
+ *   lag_den  grid step 1/lag_den samples, 1 <= lag_den <= 64.
+ *   K        rank; 0 selects the energy rule below.
+ *   energy   fraction of ||W||_F^2 the kept singular values must hold
+ *            (<= 0 selects 0.999); singular values tied with the last kept one
+ *            are kept too.
+ *   prec     an fcc_prec_t.
+ *   device   CUDA device ordinal; < 0 uses the calling thread's current device.
+ */
+typedef struct {
+    int n_mics;
+    const double *mic_xyz;
+    double fs;
+    int N;
+    double c;
+    double tau_max;
+    int lag_den;
+    int K;
+    double energy;
+    int prec;
+    int device;
+} fcc_plan_desc_t;
+
+/* Sizes of a plan; K = K_even + K_odd (even/odd bases of Eq. 6). */
+typedef struct {
+    int M, P, N, B, Q;      /* Q = N/4: the cropped basis length is Q+1 (Eq. 7) */
+    int L, den, I, center;  /* center = L*den, the index of tau = 0 */
+    int K, K_even, K_odd;
+    int prec;
+    double delta;           /* grid step 1/den */
+    double fs, c;
+} fcc_plan_info_t;
+
+typedef struct fcc_plan fcc_plan_t;
+
+/*
+ * Build the bases for one (geometry, N, grid, K, precision) key (Sec. 4,
+ * Eqs. 6-7): the even and odd halves of W are formed in FP64 on the GPU with
+ * exact argument reduction, each half gets its own FP64 one-sided Jacobi SVD on
+ * the GPU, the singular values are merged and K is chosen, and the cropped
+ * bases and the lag dictionary are packed for the kernels.  Synchronous.
+ * On success *out owns device memory until fcc_plan_destroy().
+ * Errors: INVALID_ARG (bad desc/out), UNSUPPORTED, OOM, CUDA, NOT_CONVERGED.
+ */
+fcc_status_t fcc_plan_create(const fcc_plan_desc_t *desc, fcc_plan_t **out);
+
+/* Release a plan (NULL is ignored).  Waits for the plan's device work. */
+void fcc_plan_destroy(fcc_plan_t *plan);
+
+/* Copy the plan's sizes into *info. */
+fcc_status_t fcc_plan_info(const fcc_plan_t *plan, fcc_plan_info_t *info);
+
+/* Copy the lag grid tau_0..tau_{I-1} (samples) into host taus[I]. */
+fcc_status_t fcc_plan_taus(const fcc_plan_t *plan, double *taus);
+
+/*
+ * Copy every singular value of the even block (min(I, Q+1) values) and of the
+ * odd block (min(I, Q) values), each in descending order, into host arrays
+ * s_even / s_odd (either may be NULL); their counts go to *n_even / *n_odd.
+ * Together they are the singular values of W (Sec. 4).
+ */
+fcc_status_t fcc_plan_singular_values(const fcc_plan_t *plan, double *s_even, int *n_even,
+                                      double *s_odd, int *n_odd);
+
+/*
+ * Copy the FP64 bases the kernels use (host arrays, row-major, any may be NULL):
+ *   Pe[K_even][Q+1]  cropped even projection bases p_hat_k (Eq. 7), applied to x_s;
+ *   Po[K_odd][Q]     cropped odd bases (the real q_hat with p_hat = j q_hat), applied
+ *                    to x_d (Eq. 8); entry f = Q is zero for odd bases and omitted;
+ *   Ue[I][K_even], Uo[I][K_odd]  dictionary columns (D = U_hat, Sec. 4) with the
+ *                    common phase exp(j pi tau / 2) factored out.
+ * With z_e = Pe x_s and z_o = Po x_d (complex), the correlation is
+ *   y(tau_i) = 2 Re{ exp(j pi tau_i / 2) (Ue z_e + j Uo z_o)[i] }.
+ */
+fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, double *Ue, double *Uo);
+
+/*
+ * FCC hot path (Sec. 2 PHAT -> Eq. 8 fold -> Eq. 9 projection -> reconstruction
+ * on the lag grid -> argmax -> quadratic refinement) over T frames.
+ *   d_spectra  device complex64 [T][M][B] (16-byte aligned).
+ *   T          number of frames, >= 0 (0 is a no-op).
+ *   d_lag_idx  device int32 [T][P]: argmax lag index (required).
+ *   d_peak     device float [T][P]: y at the argmax (required).
+ *   d_tau_hat  device float [T][P]: refined TDoA in samples, or NULL.
+ *   d_coeffs   device float [T][P][2K]: projection coefficients in the order
+ *              Re z_e (K_even), Im z_e (K_even), Re z_o (K_odd), Im z_o (K_odd); or NULL.
+ *   d_corr     device float [T][P][I]: the correlation y on the grid; or NULL.
+ *   stream     cudaStream_t or NULL.
+ * Asynchronous; allocates nothing.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+fcc_status_t fcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int *d_lag_idx,
+                      float *d_peak, float *d_tau_hat, float *d_coeffs, float *d_corr,
+                      void *stream);
+
+/*
+ * fcc_tdoa from and to HOST memory: the frames are streamed to the device in
+ * chunks through the plan's double-buffered staging area (allocated on the
+ * first call, about 2 x 256 MiB), overlapping host-to-device copies with the
+ * kernels; results are copied back.  Host buffers should be page-locked for
+ * full copy bandwidth.  Synchronous: returns after the results are in host
+ * memory and the device error word has been checked.
+ *   h_spectra complex64 [T][M][B]; h_lag_idx int32 [T][P]; h_peak float [T][P];
+ *   h_tau_hat float [T][P] or NULL.
+ */
+fcc_status_t fcc_tdoa_host(fcc_plan_t *plan, const void *h_spectra, long long T,
+                           int *h_lag_idx, float *h_peak, float *h_tau_hat, void *stream);
+
+/*
+ * Same-GPU GCC-PHAT baseline (Sec. 3, eq. 2 through an r-times zero-padded
+ * real inverse FFT with r = den; the DC bin, and for r = 1 the Nyquist bin, is
+ * doubled so that the values equal eq. 2 exactly): PHAT pair spectra ->
+ * batched cuFFT C2R of size rN -> gather on the lag grid -> argmax.
+ * Uses the full-rank correlation (no basis truncation).  Runs in chunks of
+ * frames through a workspace owned by the plan (created on the first call).
+ *   d_corr  device float [T][P][I] or NULL.
+ * Asynchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+fcc_status_t fcc_gcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int *d_lag_idx,
+                          float *d_peak, float *d_corr, void *stream);
+
+/*
+ * Synchronise `stream` (NULL = legacy default), then read and clear the plan's
+ * device error word: FCC_OK, FCC_ERR_NONFINITE or FCC_ERR_TIMEOUT.
+ */
+fcc_status_t fcc_plan_sync(fcc_plan_t *plan, void *stream);
+
+/* Static description of a status code. */
+const char *fcc_status_string(fcc_status_t status);
+
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char *fcc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCC_GB300_H */

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libfcc_gb300.so (the C ABI in include/fcc.h).
+
+Argument marshalling only: every step of the FCC path runs in the library's
+CUDA kernels.  PyTorch is used to allocate device / pinned-host buffers and to
+supply the current CUDA stream.  There is no CPU fallback: if the library is
+missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfcc_gb300.so")
+
+FCC_OK = 0
+STATUS = {0: "FCC_OK", 1: "FCC_ERR_INVALID_ARG", 2: "FCC_ERR_UNSUPPORTED", 3: "FCC_ERR_OOM",
+          4: "FCC_ERR_CUDA", 5: "FCC_ERR_TIMEOUT", 6: "FCC_ERR_NONFINITE", 7: "FCC_ERR_NOT_CONVERGED"}
+PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+# every symbol include/fcc.h declares
+EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_taus",
+           "fcc_plan_singular_values", "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa",
+           "fcc_plan_sync", "fcc_status_string", "fcc_last_error"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("n_mics", ctypes.c_int), ("mic_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("fs", ctypes.c_double), ("N", ctypes.c_int), ("c", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("lag_den", ctypes.c_int), ("K", ctypes.c_int),
+                ("energy", ctypes.c_double), ("prec", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("P", ctypes.c_int), ("N", ctypes.c_int), ("B", ctypes.c_int),
+                ("Q", ctypes.c_int), ("L", ctypes.c_int), ("den", ctypes.c_int), ("I", ctypes.c_int),
+                ("center", ctypes.c_int), ("K", ctypes.c_int), ("K_even", ctypes.c_int),
+                ("K_odd", ctypes.c_int), ("prec", ctypes.c_int), ("delta", ctypes.c_double),
+                ("fs", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class FccError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.fcc_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(_vp)]
+        L.fcc_plan_destroy.argtypes = [_vp]
+        L.fcc_plan_destroy.restype = None
+        L.fcc_plan_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+        L.fcc_plan_taus.argtypes = [_vp, _dp]
+        L.fcc_plan_singular_values.argtypes = [_vp, _dp, _ip, _dp, _ip]
+        L.fcc_plan_bases.argtypes = [_vp, _dp, _dp, _dp, _dp]
+        L.fcc_tdoa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.fcc_tdoa_host.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
+        L.fcc_gcc_tdoa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
+        L.fcc_plan_sync.argtypes = [_vp, _vp]
+        L.fcc_status_string.argtypes = [ctypes.c_int]
+        L.fcc_status_string.restype = ctypes.c_char_p
+        L.fcc_last_error.argtypes = []
+        L.fcc_last_error.restype = ctypes.c_char_p
+        for name in ("fcc_plan_create", "fcc_plan_info", "fcc_plan_taus", "fcc_plan_singular_values",
+                     "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa", "fcc_plan_sync"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(status: int, where: str):
+    if status != FCC_OK:
+        raise FccError(status, where, lib().fcc_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """An FCC plan: lag grid, rank-K even/odd bases and kernel tables on one GPU."""
+
+    def __init__(self, n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0,
+                 mic_xyz=None, c: float = 343.0, K: int = 0, energy: float = 0.999,
+                 prec: str = "fp32", device: int | None = None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        xyz = None
+        if mic_xyz is not None:
+            xyz = np.ascontiguousarray(mic_xyz, np.float64).reshape(n_mics, 3)
+        desc = PlanDesc(n_mics, xyz.ctypes.data_as(_dp) if xyz is not None else None, float(fs), int(N),
+                        float(c), float(tau_max), int(lag_den), int(K), float(energy), PREC[prec],
+                        self.device)
+        h = _vp()
+        check(lib().fcc_plan_create(ctypes.byref(desc), ctypes.byref(h)), "fcc_plan_create")
+        self._h = h
+        info = PlanInfo()
+        check(lib().fcc_plan_info(h, ctypes.byref(info)), "fcc_plan_info")
+        self.info = {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+
+    def __getattr__(self, name):
+        info = self.__dict__.get("info")
+        if info is not None and name in info:
+            return info[name]
+        raise AttributeError(name)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fcc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host-side queries
+    def taus(self) -> np.ndarray:
+        out = np.empty(self.I)
+        check(lib().fcc_plan_taus(self._h, out.ctypes.data_as(_dp)), "fcc_plan_taus")
+        return out
+
+    def singular_values(self):
+        ne, no = ctypes.c_int(), ctypes.c_int()
+        check(lib().fcc_plan_singular_values(self._h, None, ctypes.byref(ne), None, ctypes.byref(no)),
+              "fcc_plan_singular_values")
+        se, so = np.empty(ne.value), np.empty(no.value)
+        check(lib().fcc_plan_singular_values(self._h, se.ctypes.data_as(_dp), None,
+                                             so.ctypes.data_as(_dp), None), "fcc_plan_singular_values")
+        return se, so
+
+    def bases(self):
+        KE, KO, Q, I = self.K_even, self.K_odd, self.Q, self.I
+        Pe, Po = np.empty((KE, Q + 1)), np.empty((KO, Q))
+        Ue, Uo = np.empty((I, KE)), np.empty((I, KO))
+        check(lib().fcc_plan_bases(self._h, Pe.ctypes.data_as(_dp), Po.ctypes.data_as(_dp),
+                                   Ue.ctypes.data_as(_dp), Uo.ctypes.data_as(_dp)), "fcc_plan_bases")
+        return Pe, Po, Ue, Uo
+
+    # ---- device entry points
+    def _check_spectra(self, X):
+        import torch
+        if X.dtype != torch.complex64 or X.dim() != 3 or X.shape[1] != self.M or X.shape[2] != self.B:
+            raise ValueError(f"spectra must be complex64 [T, {self.M}, {self.B}]")
+        if not X.is_contiguous():
+            raise ValueError("spectra must be contiguous")
+
+    def tdoa(self, X, tau_hat: bool = True, coeffs: bool = False, corr: bool = False, stream=None,
+             out=None):
+        """FCC on device spectra X [T, M, B] (complex64): dict of device tensors."""
+        import torch
+        self._check_spectra(X)
+        T = X.shape[0]
+        dev = X.device
+        if out is None:
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, device=dev),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, device=dev)}
+            if tau_hat:
+                out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, device=dev)
+            if coeffs:
+                out["coeffs"] = torch.empty((T, self.P, 2 * self.K), dtype=torch.float32, device=dev)
+            if corr:
+                out["corr"] = torch.empty((T, self.P, self.I), dtype=torch.float32, device=dev)
+        check(lib().fcc_tdoa(self._h, _ptr(X), T, _ptr(out["lag_idx"]), _ptr(out["peak"]),
+                             _ptr(out.get("tau_hat")), _ptr(out.get("coeffs")), _ptr(out.get("corr")),
+                             _stream(stream, dev)), "fcc_tdoa")
+        return out
+
+    def tdoa_host(self, X_host, tau_hat: bool = True, out=None, stream=None):
+        """FCC from host spectra to host results (pinned host memory recommended)."""
+        import torch
+        self._check_spectra(X_host)
+        T = X_host.shape[0]
+        if out is None:
+            pin = X_host.is_pinned()
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, pin_memory=pin),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, pin_memory=pin)}
+            if tau_hat:
+                out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, pin_memory=pin)
+        check(lib().fcc_tdoa_host(self._h, _ptr(X_host), T, _ptr(out["lag_idx"]), _ptr(out["peak"]),
+                                  _ptr(out.get("tau_hat")), _stream(stream, self.device)), "fcc_tdoa_host")
+        return out
+
+    def gcc_tdoa(self, X, corr: bool = False, stream=None, out=None):
+        """Same-GPU GCC-PHAT baseline (full rank, r = den) on device spectra."""
+        import torch
+        self._check_spectra(X)
+        T = X.shape[0]
+        dev = X.device
+        if out is None:
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, device=dev),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, device=dev)}
+            if corr:
+                out["corr"] = torch.empty((T, self.P, self.I), dtype=torch.float32, device=dev)
+        check(lib().fcc_gcc_tdoa(self._h, _ptr(X), T, _ptr(out["lag_idx"]), _ptr(out["peak"]),
+                                 _ptr(out.get("corr")), _stream(stream, dev)), "fcc_gcc_tdoa")
+        return out
+
+    def sync(self, stream=None):
+        """Synchronise and raise if a kernel latched an error (NaN/Inf input, timeout)."""
+        check(lib().fcc_plan_sync(self._h, _stream(stream, self.device)), "fcc_plan_sync")

@@ -1,0 +1,411 @@
+// fcc_api.cu -- the extern "C" entry points declared in include/fcc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fcc_internal.h"
+
+namespace fcc {
+
+static thread_local std::string g_last_error;
+
+fcc_status_t fail(fcc_status_t st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+fcc_status_t cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FCC_ERR_OOM : FCC_ERR_CUDA;
+}
+
+namespace {
+
+// Makes `dev` current for the scope of one entry point and restores the
+// caller's device afterwards.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int pair_index(int M, int i, int j) { return i * M - i * (i + 1) / 2 + (j - i - 1); }
+
+// Tile the pair triangle into 2x2 blocks of microphone groups {2a, 2a+1}:
+// off-diagonal blocks carry up to 4 pairs; the one pair inside each group is
+// collected two groups at a time.
+std::vector<Slot> make_slots(int M)
+{
+    std::vector<Slot> out;
+    const int G = (M + 1) / 2;
+    auto mic = [&](int g, int r) { return 2 * g + r < M ? 2 * g + r : -1; };
+    for (int a = 0; a < G; ++a)
+        for (int b = a + 1; b < G; ++b) {
+            int m[4] = {mic(a, 0), mic(a, 1), mic(b, 0), mic(b, 1)};
+            Slot s;
+            for (int q = 0; q < 4; ++q) {
+                int i = m[q >> 1], j = m[2 + (q & 1)];
+                s.pair[q] = (i >= 0 && j >= 0) ? pair_index(M, i, j) : -1;
+            }
+            for (int r = 0; r < 4; ++r) s.mic[r] = m[r] >= 0 ? m[r] : m[r & 2];
+            out.push_back(s);
+        }
+    std::vector<int> diag;
+    for (int a = 0; a < G; ++a)
+        if (mic(a, 1) >= 0) diag.push_back(a);
+    for (size_t k = 0; k < diag.size(); k += 2) {
+        int a = diag[k], b = (k + 1 < diag.size()) ? diag[k + 1] : -1;
+        Slot s;
+        s.mic[0] = 2 * a;
+        s.mic[2] = 2 * a + 1;
+        s.mic[1] = b >= 0 ? 2 * b : 2 * a;
+        s.mic[3] = b >= 0 ? 2 * b + 1 : 2 * a + 1;
+        s.pair[0] = pair_index(M, 2 * a, 2 * a + 1);
+        s.pair[1] = -1;
+        s.pair[2] = -1;
+        s.pair[3] = b >= 0 ? pair_index(M, 2 * b, 2 * b + 1) : -1;
+        out.push_back(s);
+    }
+    return out;
+}
+
+// FP32 tables for the kernel:
+//   basis [Q+1][2 kh]: row f = (Pe[0..KE)(f), 0.., Po[0..KO)(f), 0..), Po(Q) = 0;
+//   recon [center+1][4][kh]: for tau = m/den >= 0, a = cos(pi tau/2), b = sin(pi tau/2),
+//     gSe = 2a Ue(tau), gSo = -2b Uo(tau), gDe = 2b Ue(tau), gDo = 2a Uo(tau), so that
+//     y(+tau) = S - D and y(-tau) = S + D with S = gSe.Re z_e + gSo.Re z_o and
+//     D = gDe.Im z_e + gDo.Im z_o (Ue even and Uo odd in tau).
+void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<float> &recon)
+{
+    const fcc_plan_info_t &in = plan->info;
+    const int kh = plan->kh, Q = in.Q, KE = in.K_even, KO = in.K_odd;
+    basis.assign((size_t)(Q + 1) * 2 * kh, 0.f);
+    for (int f = 0; f <= Q; ++f) {
+        for (int k = 0; k < KE; ++k) basis[(size_t)f * 2 * kh + k] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
+        if (f < Q)
+            for (int k = 0; k < KO; ++k) basis[(size_t)f * 2 * kh + kh + k] = (float)plan->Po[(size_t)k * Q + f];
+    }
+    recon.assign((size_t)(in.center + 1) * 4 * kh, 0.f);
+    for (int m = 0; m <= in.center; ++m) {
+        const int i = in.center + m;
+        const double ang = M_PI * 0.5 * (double)m / (double)in.den;
+        const double a = std::cos(ang), b = std::sin(ang);
+        float *g = &recon[(size_t)m * 4 * kh];
+        for (int k = 0; k < KE; ++k) {
+            const double u = plan->Ue[(size_t)i * KE + k];
+            g[k] = (float)(2.0 * a * u);
+            g[2 * kh + k] = (float)(2.0 * b * u);
+        }
+        for (int k = 0; k < KO; ++k) {
+            const double u = plan->Uo[(size_t)i * KO + k];
+            g[kh + k] = (float)(-2.0 * b * u);
+            g[3 * kh + k] = (float)(2.0 * a * u);
+        }
+    }
+}
+
+void free_plan(fcc_plan *p)
+{
+    if (!p) return;
+    cudaFree(p->d_basis);
+    cudaFree(p->d_recon);
+    cudaFree(p->d_slots);
+    cudaFree(p->d_err);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->d_stage[b]);
+        cudaFree(p->d_stage_idx[b]);
+        cudaFree(p->d_stage_peak[b]);
+        cudaFree(p->d_stage_tau[b]);
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    for (auto &e : p->ev)
+        if (e) cudaEventDestroy(e);
+    gcc_destroy(p);
+    delete p;
+}
+
+}  // namespace
+}  // namespace fcc
+
+using namespace fcc;
+
+extern "C" {
+
+const char *fcc_status_string(fcc_status_t s)
+{
+    switch (s) {
+    case FCC_OK: return "ok";
+    case FCC_ERR_INVALID_ARG: return "invalid argument";
+    case FCC_ERR_UNSUPPORTED: return "unsupported";
+    case FCC_ERR_OOM: return "out of memory";
+    case FCC_ERR_CUDA: return "CUDA error";
+    case FCC_ERR_TIMEOUT: return "device wait timed out";
+    case FCC_ERR_NONFINITE: return "non-finite input";
+    case FCC_ERR_NOT_CONVERGED: return "SVD did not converge";
+    }
+    return "unknown status";
+}
+
+const char *fcc_last_error(void) { return g_last_error.c_str(); }
+
+fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
+{
+    g_last_error.clear();
+    if (!d || !out) return fail(FCC_ERR_INVALID_ARG, "null desc or out");
+    *out = nullptr;
+    if (d->n_mics < 2) return fail(FCC_ERR_INVALID_ARG, "n_mics < 2");
+    if (d->n_mics > 16) return fail(FCC_ERR_UNSUPPORTED, "n_mics > 16");
+    if (!(d->fs > 0)) return fail(FCC_ERR_INVALID_ARG, "fs <= 0");
+    if (d->N < 16 || d->N > 4096 || (d->N & (d->N - 1)))
+        return fail(FCC_ERR_INVALID_ARG, "N must be a power of two in [16, 4096]");
+    if (d->lag_den < 1 || d->lag_den > 64) return fail(FCC_ERR_INVALID_ARG, "lag_den out of [1, 64]");
+    if (d->prec < FCC_PREC_FP32 || d->prec > FCC_PREC_FP16) return fail(FCC_ERR_INVALID_ARG, "prec");
+    if (d->prec != FCC_PREC_FP32) return fail(FCC_ERR_UNSUPPORTED, "only FCC_PREC_FP32 in this build");
+    if (d->K < 0) return fail(FCC_ERR_INVALID_ARG, "K < 0");
+    const double c = d->c > 0 ? d->c : 343.0;
+    int L;
+    if (d->tau_max > 0) {
+        L = (int)std::ceil(d->tau_max - 1e-9);
+    } else {
+        if (!d->mic_xyz) return fail(FCC_ERR_INVALID_ARG, "tau_max <= 0 needs mic_xyz");
+        double dmax = 0;
+        for (int i = 0; i < d->n_mics; ++i)
+            for (int j = i + 1; j < d->n_mics; ++j) {
+                double s = 0;
+                for (int k = 0; k < 3; ++k) {
+                    double t = d->mic_xyz[3 * i + k] - d->mic_xyz[3 * j + k];
+                    s += t * t;
+                }
+                dmax = std::max(dmax, std::sqrt(s));
+            }
+        L = (int)std::ceil(dmax * d->fs / c - 1e-9);
+    }
+    if (L < 1) return fail(FCC_ERR_INVALID_ARG, "lag half-range must be at least one sample");
+    const int I = 2 * L * d->lag_den + 1;
+    if (I > 1025) return fail(FCC_ERR_UNSUPPORTED, "more than 1025 lag candidates");
+    if (L * 2 > d->N / 2) return fail(FCC_ERR_INVALID_ARG, "lag range too large for N");
+
+    int dev = d->device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(FCC_ERR_CUDA, "no CUDA device");
+    DeviceScope scope(dev);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    fcc_plan *p = new (std::nothrow) fcc_plan();
+    if (!p) return fail(FCC_ERR_OOM, "host allocation");
+    p->device = dev;
+    fcc_plan_info_t &in = p->info;
+    in.M = d->n_mics;
+    in.P = in.M * (in.M - 1) / 2;
+    in.N = d->N;
+    in.B = d->N / 2 + 1;
+    in.Q = d->N / 4;
+    in.L = L;
+    in.den = d->lag_den;
+    in.I = I;
+    in.center = L * d->lag_den;
+    in.prec = d->prec;
+    in.delta = 1.0 / d->lag_den;
+    in.fs = d->fs;
+    in.c = c;
+    p->taus.resize(I);
+    for (int i = 0; i < I; ++i) p->taus[i] = (double)(i - in.center) / (double)in.den;
+    cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    fcc_status_t st = build_plan_bases(p, d->K, d->energy > 0 ? d->energy : 0.999);
+    if (st != FCC_OK) {
+        free_plan(p);
+        return st;
+    }
+    const int kmax = std::max(in.K_even, in.K_odd);
+    p->kh = kmax <= 2 ? 2 : kmax <= 4 ? 4 : kmax <= 6 ? 6 : kmax <= 8 ? 8 : 0;
+    std::vector<Slot> slots = make_slots(in.M);
+    p->n_slots = (int)slots.size();
+    if (p->kh) {
+        st = choose_fp32_geometry(p);
+        if (st != FCC_OK) {
+            free_plan(p);
+            return st;
+        }
+        std::vector<float> basis, recon;
+        pack_tables(p, basis, recon);
+        e = cudaMalloc(&p->d_basis, basis.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_recon, recon.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_basis, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_recon, recon.data(), recon.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_slots, slots.size() * sizeof(Slot));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_slots, slots.data(), slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "plan tables");
+    }
+    *out = p;
+    return FCC_OK;
+}
+
+void fcc_plan_destroy(fcc_plan_t *plan)
+{
+    if (!plan) return;
+    DeviceScope scope(plan->device);
+    cudaDeviceSynchronize();
+    free_plan(plan);
+}
+
+fcc_status_t fcc_plan_info(const fcc_plan_t *plan, fcc_plan_info_t *info)
+{
+    if (!plan || !info) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    *info = plan->info;
+    return FCC_OK;
+}
+
+fcc_status_t fcc_plan_taus(const fcc_plan_t *plan, double *taus)
+{
+    if (!plan || !taus) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    std::copy(plan->taus.begin(), plan->taus.end(), taus);
+    return FCC_OK;
+}
+
+fcc_status_t fcc_plan_singular_values(const fcc_plan_t *plan, double *s_even, int *n_even, double *s_odd,
+                                      int *n_odd)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (n_even) *n_even = (int)plan->s_even.size();
+    if (n_odd) *n_odd = (int)plan->s_odd.size();
+    if (s_even) std::copy(plan->s_even.begin(), plan->s_even.end(), s_even);
+    if (s_odd) std::copy(plan->s_odd.begin(), plan->s_odd.end(), s_odd);
+    return FCC_OK;
+}
+
+fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, double *Ue, double *Uo)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (Pe) std::copy(plan->Pe.begin(), plan->Pe.end(), Pe);
+    if (Po) std::copy(plan->Po.begin(), plan->Po.end(), Po);
+    if (Ue) std::copy(plan->Ue.begin(), plan->Ue.end(), Ue);
+    if (Uo) std::copy(plan->Uo.begin(), plan->Uo.end(), Uo);
+    return FCC_OK;
+}
+
+fcc_status_t fcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int *d_lag_idx, float *d_peak,
+                      float *d_tau_hat, float *d_coeffs, float *d_corr, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (T < 0) return fail(FCC_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return FCC_OK;
+    if (!d_spectra || !d_lag_idx || !d_peak) return fail(FCC_ERR_INVALID_ARG, "null spectra/lag_idx/peak");
+    if (reinterpret_cast<uintptr_t>(d_spectra) & 15) return fail(FCC_ERR_INVALID_ARG, "spectra not 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(d_lag_idx) | reinterpret_cast<uintptr_t>(d_peak) |
+         reinterpret_cast<uintptr_t>(d_tau_hat) | reinterpret_cast<uintptr_t>(d_coeffs) |
+         reinterpret_cast<uintptr_t>(d_corr)) & 3)
+        return fail(FCC_ERR_INVALID_ARG, "output not 4-byte aligned");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    return launch_fp32(plan, static_cast<const float2 *>(d_spectra), T, d_lag_idx, d_peak, d_tau_hat, d_coeffs,
+                       d_corr, static_cast<cudaStream_t>(stream));
+}
+
+fcc_status_t fcc_plan_sync(fcc_plan_t *plan, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    DeviceScope scope(plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FCC_CUDA_TRY(cudaStreamSynchronize(st));
+    unsigned err = 0;
+    FCC_CUDA_TRY(cudaMemcpyAsync(&err, plan->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    FCC_CUDA_TRY(cudaMemsetAsync(plan->d_err, 0, sizeof(unsigned), st));
+    FCC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (err & kErrTimeout) return fail(FCC_ERR_TIMEOUT, "a device-side wait expired");
+    if (err & kErrNonFinite) return fail(FCC_ERR_NONFINITE, "NaN or Inf in the spectra");
+    return FCC_OK;
+}
+
+fcc_status_t fcc_tdoa_host(fcc_plan_t *plan, const void *h_spectra, long long T, int *h_lag_idx,
+                           float *h_peak, float *h_tau_hat, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (T < 0) return fail(FCC_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return FCC_OK;
+    if (!h_spectra || !h_lag_idx || !h_peak) return fail(FCC_ERR_INVALID_ARG, "null host buffer");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    const fcc_plan_info_t &in = plan->info;
+    const size_t frame_bytes = (size_t)in.M * in.B * 8;
+    if (!plan->d_stage[0]) {
+        long long chunk = std::max<long long>(1, (256LL << 20) / (long long)frame_bytes);
+        for (int b = 0; b < 2; ++b) {
+            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage[b], chunk * frame_bytes));
+            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_idx[b], chunk * in.P * sizeof(int)));
+            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_peak[b], chunk * in.P * sizeof(float)));
+            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_tau[b], chunk * in.P * sizeof(float)));
+        }
+        FCC_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+        for (auto &ev : plan->ev) FCC_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        plan->stage_frames = chunk;
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaStream_t hs = plan->copy_stream;
+    // ev[b]: H2D of buffer b done; ev[2+b]: buffer b free again (kernel and D2H done)
+    FCC_CUDA_TRY(cudaEventRecord(plan->ev[4], cs));
+    FCC_CUDA_TRY(cudaStreamWaitEvent(hs, plan->ev[4], 0));
+    const char *src = static_cast<const char *>(h_spectra);
+    long long chunk_id = 0;
+    for (long long t0 = 0; t0 < T; t0 += plan->stage_frames, ++chunk_id) {
+        const int b = (int)(chunk_id & 1);
+        const long long n = std::min(plan->stage_frames, T - t0);
+        if (chunk_id >= 2) FCC_CUDA_TRY(cudaStreamWaitEvent(hs, plan->ev[2 + b], 0));
+        FCC_CUDA_TRY(cudaMemcpyAsync(plan->d_stage[b], src + (size_t)t0 * frame_bytes, (size_t)n * frame_bytes,
+                                     cudaMemcpyHostToDevice, hs));
+        FCC_CUDA_TRY(cudaEventRecord(plan->ev[b], hs));
+        FCC_CUDA_TRY(cudaStreamWaitEvent(cs, plan->ev[b], 0));
+        fcc_status_t st = launch_fp32(plan, static_cast<const float2 *>(plan->d_stage[b]), n, plan->d_stage_idx[b],
+                                      plan->d_stage_peak[b], h_tau_hat ? plan->d_stage_tau[b] : nullptr, nullptr,
+                                      nullptr, cs);
+        if (st != FCC_OK) return st;
+        const size_t o = (size_t)t0 * in.P, cnt = (size_t)n * in.P;
+        FCC_CUDA_TRY(cudaMemcpyAsync(h_lag_idx + o, plan->d_stage_idx[b], cnt * sizeof(int), cudaMemcpyDeviceToHost, cs));
+        FCC_CUDA_TRY(cudaMemcpyAsync(h_peak + o, plan->d_stage_peak[b], cnt * sizeof(float), cudaMemcpyDeviceToHost, cs));
+        if (h_tau_hat)
+            FCC_CUDA_TRY(cudaMemcpyAsync(h_tau_hat + o, plan->d_stage_tau[b], cnt * sizeof(float),
+                                         cudaMemcpyDeviceToHost, cs));
+        FCC_CUDA_TRY(cudaEventRecord(plan->ev[2 + b], cs));
+    }
+    return fcc_plan_sync(plan, stream);
+}
+
+fcc_status_t fcc_gcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int *d_lag_idx, float *d_peak,
+                          float *d_corr, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (T < 0) return fail(FCC_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return FCC_OK;
+    if (!d_spectra || !d_lag_idx || !d_peak) return fail(FCC_ERR_INVALID_ARG, "null spectra/lag_idx/peak");
+    if (reinterpret_cast<uintptr_t>(d_spectra) & 15) return fail(FCC_ERR_INVALID_ARG, "spectra not 16-byte aligned");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    return gcc_run(plan, static_cast<const float2 *>(d_spectra), T, d_lag_idx, d_peak, d_corr,
+                   static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

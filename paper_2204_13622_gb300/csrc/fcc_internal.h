@@ -1,0 +1,109 @@
+// fcc_internal.h -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fcc.h"
+
+namespace fcc {
+
+// Device error word bits (latched by kernels, read by fcc_plan_sync).
+enum : unsigned {
+    kErrNonFinite = 1u,
+    kErrTimeout = 2u,
+};
+
+// Records a detail message for fcc_last_error() and returns `st`.
+fcc_status_t fail(fcc_status_t st, const std::string &msg);
+fcc_status_t cuda_fail(cudaError_t e, const char *what);
+
+#define FCC_CUDA_TRY(call)                                          \
+    do {                                                            \
+        cudaError_t e__ = (call);                                   \
+        if (e__ != cudaSuccess) return ::fcc::cuda_fail(e__, #call); \
+    } while (0)
+
+// One work slot of the FP32 kernel: a 2x2 block of the pair triangle,
+// mics {i1, i2} x {j1, j2}; pair[q] is the output pair index of
+// (i1,j1), (i1,j2), (i2,j1), (i2,j2) or -1 when that product is not a pair.
+struct Slot {
+    int mic[4];   // i1, i2, j1, j2
+    int pair[4];
+};
+
+// Launch geometry of the FP32 kernel, chosen on the host per plan.
+struct Fp32Geometry {
+    int C;            // frequency chunks per slot (lanes that share one slot)
+    int lanes_frame;  // n_slots * C
+    int GW;           // warps per group
+    int G;            // groups per CTA
+    int F;            // frames per stage (tile)
+    int S;            // stages in the shared-memory ring
+    int rot;          // chunk-dependent rotation of the frequency loop (bank spread)
+    size_t smem_bytes;
+};
+
+// Kernel parameters of the FP32 path (passed by value).
+struct Fp32Params {
+    const float2 *spectra;  // [T][M][B]
+    long long T;
+    int M, B, Q, N, P;
+    int n_slots, C, lanes_frame, GW, G, F, S, rot;
+    int n_tiles;
+    int frame_floats;       // M * B * 2
+    int bulk;               // 1: cp.async.bulk staging, 0: plain-load staging
+    int center, I, KE, KO;  // KE/KO: actual basis counts (<= KH)
+    float tau0, delta;
+    const float *basis;     // [Q+1][2*KH]: even bases then odd bases per bin
+    const float *recon;     // [center+1][4][KH]: gSe, gSo, gDe, gDo
+    const Slot *slots;      // [n_slots]
+    int *out_idx;
+    float *out_peak;
+    float *out_tau;         // nullable
+    float *out_coef;        // nullable, [T][P][2K]
+    float *out_corr;        // nullable, [T][P][I]
+    unsigned *err;
+};
+
+}  // namespace fcc
+
+// The plan object behind the opaque ABI handle.
+struct fcc_plan {
+    fcc_plan_info_t info{};
+    int device = 0;
+    int kh = 0;                    // padded basis count per parity (template instance)
+    std::vector<double> taus;      // [I]
+    std::vector<double> s_even, s_odd;
+    std::vector<double> Pe, Po, Ue, Uo;  // FP64 bases as used (see fcc_plan_bases)
+    // device
+    float *d_basis = nullptr;
+    float *d_recon = nullptr;
+    fcc::Slot *d_slots = nullptr;
+    unsigned *d_err = nullptr;
+    int n_slots = 0;
+    fcc::Fp32Geometry geo{};
+    int num_sms = 0;
+    // host-streaming staging (fcc_tdoa_host), created lazily
+    void *d_stage[2] = {nullptr, nullptr};
+    int *d_stage_idx[2] = {nullptr, nullptr};
+    float *d_stage_peak[2] = {nullptr, nullptr};
+    float *d_stage_tau[2] = {nullptr, nullptr};
+    long long stage_frames = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev[6] = {};
+    // GCC baseline workspace, created lazily
+    void *gcc_state = nullptr;
+};
+
+namespace fcc {
+fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy);
+fcc_status_t choose_fp32_geometry(fcc_plan *plan);
+fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,
+                         float *peak, float *tau, float *coef, float *corr, cudaStream_t st);
+fcc_status_t gcc_run(fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                     float *corr, cudaStream_t st);
+void gcc_destroy(fcc_plan *plan);
+}  // namespace fcc

@@ -1,0 +1,270 @@
+// fcc_plan.cu -- basis construction for one plan key (Sec. 4, Eqs. 6-7).
+//
+// W(i,f) = exp(j 2 pi f tau_i / N) (Eq. 3).  With g = f - N/4 and phi_i =
+// exp(j pi tau_i / 2), W = diag(phi) (C + j S) where C(i,g) = cos(2 pi g tau_i/N)
+// is even in g and S(i,g) = sin(2 pi g tau_i / N) is odd in g.  For a grid that
+// is symmetric about 0, W^H W = C^T C + S^T S, so the right singular vectors of
+// W split into functions even about f = N/4 (those of C) and odd ones (those
+// of S) -- the parity property of Eq. 6.  Folding x with the orthonormal maps
+//   F_e: x -> [(x(f) + x(N/2-f))/sqrt2 for f < N/4,  x(N/4)]   (Eq. 8, x_s)
+//   F_o: x -> [(x(f) - x(N/2-f))/sqrt2 for f < N/4]            (Eq. 8, x_d)
+// gives two small real matrices, one per parity,
+//   A_e(i,f) = w_f cos(2 pi (f - N/4) tau_i / N),  w_f = sqrt2 (f < N/4), 1 (f = N/4)
+//   A_o(i,f) = sqrt2 sin(2 pi (f - N/4) tau_i / N),  f < N/4,
+// whose singular values together are those of W.  Each is decomposed here by
+// an FP64 one-sided Jacobi SVD (Hestenes 1958; parallel round-robin ordering as
+// in Brent & Luk 1985) on the GPU, one CTA per block.  The host then merges the
+// two spectra, picks K, and packs the cropped bases p_hat (Eq. 7) and the lag
+// dictionary for the kernels.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "fcc_internal.h"
+
+namespace fcc {
+namespace {
+
+constexpr int kJacobiThreads = 1024;
+constexpr int kMaxSweeps = 60;
+
+// cos/sin of pi * n / d for integers n, d > 0, with n reduced exactly mod 2d
+// so that the FP64 sincospi call sees an argument in [0, 2).
+__device__ __forceinline__ void sincospi_ratio(long long n, long long d, double *s, double *c)
+{
+    long long p = 2 * d;
+    long long r = n % p;
+    if (r < 0) r += p;
+    sincospi((double)r / (double)d, s, c);
+}
+
+// A_e [I][Q+1] and A_o [I][Q]; tau_i = (i - L den)/den, so
+// 2 pi (f - Q) tau_i / N = pi * 2 (f - Q) (i - L den) / (den N).
+__global__ void build_halves_kernel(int I, int Ld, int den, int N, int Q, double *Ae, double *Ao)
+{
+    int i = blockIdx.y;
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I || f > Q) return;
+    long long m = (long long)i - Ld;
+    long long num = 2LL * (f - Q) * m;
+    double s, c;
+    sincospi_ratio(num, (long long)den * N, &s, &c);
+    const double r2 = 1.4142135623730950488;
+    Ae[(size_t)i * (Q + 1) + f] = (f < Q ? r2 : 1.0) * c;
+    if (f < Q) Ao[(size_t)i * Q + f] = r2 * s;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One-sided Jacobi on the n row vectors x_k (length len) of X [n][len]:
+// rotations x_p <- c x_p - s x_q, x_q <- s x_p + c x_q make the rows mutually
+// orthogonal; the same rotations applied to J (identity at start, row k holding
+// column k of the accumulated orthogonal matrix) give X_0^T J^T... i.e. with
+// A = X_0 (I x len), A = J^T-columns * Y: A = sum_k J[k][:]^T y_k^T.
+// Block b of the grid works on matrix b.
+struct JacobiJob {
+    double *X;
+    double *J;
+    int n, len;
+    int *sweeps;  // out: sweeps used, or -1 if not converged
+};
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_svd_kernel(JacobiJob j0, JacobiJob j1,
+                                                                    double tiny2)
+{
+    JacobiJob job = blockIdx.x == 0 ? j0 : j1;
+    const int n = job.n, len = job.len;
+    double *X = job.X, *J = job.J;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) J[e] = (e / n == e % n) ? 1.0 : 0.0;
+    __shared__ int rotated;
+    const int np = n + (n & 1);  // players in the round-robin, one phantom if n is odd
+    int sweep = 0;
+    bool done = false;
+    __syncthreads();
+    for (; sweep < kMaxSweeps && !done; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < np - 1; ++r) {
+            for (int k = warp; k < np / 2; k += nwarps) {
+                int p, q;
+                if (k == 0) {
+                    p = 0;
+                    q = r % (np - 1) + 1;
+                } else {
+                    p = (r + k) % (np - 1) + 1;
+                    q = ((r - k) % (np - 1) + (np - 1)) % (np - 1) + 1;
+                }
+                if (p >= n || q >= n) continue;
+                double *xp = X + (size_t)p * len, *xq = X + (size_t)q * len;
+                double a = 0, b = 0, g = 0;
+                for (int t = lane; t < len; t += 32) {
+                    double u = xp[t], v = xq[t];
+                    a = fma(u, u, a);
+                    b = fma(v, v, b);
+                    g = fma(u, v, g);
+                }
+                a = warp_sum(a);
+                b = warp_sum(b);
+                g = warp_sum(g);
+                // skip pairs already orthogonal to working precision and pairs
+                // holding a vector that is negligible against ||A||_F
+                if (a <= tiny2 || b <= tiny2 || fabs(g) <= 1e-15 * sqrt(a * b)) continue;
+                double zeta = (b - a) / (2.0 * g);
+                double t_ = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+                double c = 1.0 / sqrt(1.0 + t_ * t_), s = c * t_;
+                for (int t = lane; t < len; t += 32) {
+                    double u = xp[t], v = xq[t];
+                    xp[t] = c * u - s * v;
+                    xq[t] = s * u + c * v;
+                }
+                double *jp = J + (size_t)p * n, *jq = J + (size_t)q * n;
+                for (int t = lane; t < n; t += 32) {
+                    double u = jp[t], v = jq[t];
+                    jp[t] = c * u - s * v;
+                    jq[t] = s * u + c * v;
+                }
+                if (lane == 0) rotated = 1;
+            }
+            __syncthreads();
+        }
+        done = (rotated == 0);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *job.sweeps = done ? sweep : -1;
+}
+
+struct Vec {
+    double sigma;
+    int parity;  // 0 even, 1 odd
+    int idx;     // row within its block
+};
+
+}  // namespace
+
+fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
+{
+    fcc_plan_info_t &in = plan->info;
+    const int I = in.I, Q = in.Q, nE = Q + 1, nO = Q;
+    double *d_Ae = nullptr, *d_Ao = nullptr, *d_Je = nullptr, *d_Jo = nullptr;
+    int *d_sw = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(d_Ae);
+        cudaFree(d_Ao);
+        cudaFree(d_Je);
+        cudaFree(d_Jo);
+        cudaFree(d_sw);
+    };
+    size_t bytes = sizeof(double) * ((size_t)I * nE + (size_t)I * nO + 2 * (size_t)I * I);
+    if (cudaMalloc(&d_Ae, sizeof(double) * (size_t)I * nE) != cudaSuccess ||
+        cudaMalloc(&d_Ao, sizeof(double) * (size_t)I * nO) != cudaSuccess ||
+        cudaMalloc(&d_Je, sizeof(double) * (size_t)I * I) != cudaSuccess ||
+        cudaMalloc(&d_Jo, sizeof(double) * (size_t)I * I) != cudaSuccess ||
+        cudaMalloc(&d_sw, 2 * sizeof(int)) != cudaSuccess) {
+        cleanup();
+        (void)cudaGetLastError();
+        return fail(FCC_ERR_OOM, "plan workspace (" + std::to_string(bytes) + " bytes)");
+    }
+    dim3 gb((nE + 127) / 128, I);
+    build_halves_kernel<<<gb, 128>>>(I, in.L * in.den, in.den, in.N, Q, d_Ae, d_Ao);
+    // ||A||_F^2 = I (N/2 + 1) per block at most; vectors below 1e-30 of it are noise
+    double tiny2 = 1e-30 * (double)I * (double)(in.N / 2 + 1);
+    JacobiJob je{d_Ae, d_Je, I, nE, d_sw};
+    JacobiJob jo{d_Ao, d_Jo, I, nO, d_sw + 1};
+    jacobi_svd_kernel<<<2, kJacobiThreads>>>(je, jo, tiny2);
+    std::vector<double> Xe((size_t)I * nE), Xo((size_t)I * nO), Je((size_t)I * I), Jo((size_t)I * I);
+    int sw[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(Xe.data(), d_Ae, sizeof(double) * Xe.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(Xo.data(), d_Ao, sizeof(double) * Xo.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(Je.data(), d_Je, sizeof(double) * Je.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(Jo.data(), d_Jo, sizeof(double) * Jo.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sw, d_sw, sizeof(sw), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "plan basis construction");
+    if (sw[0] < 0 || sw[1] < 0) return fail(FCC_ERR_NOT_CONVERGED, "Jacobi SVD did not converge");
+
+    // singular values = row norms of the rotated matrices
+    auto norms = [](const std::vector<double> &X, int n, int len) {
+        std::vector<double> s(n);
+        for (int k = 0; k < n; ++k) {
+            double a = 0;
+            for (int t = 0; t < len; ++t) a += X[(size_t)k * len + t] * X[(size_t)k * len + t];
+            s[k] = std::sqrt(a);
+        }
+        return s;
+    };
+    std::vector<double> se = norms(Xe, I, nE), so = norms(Xo, I, nO);
+    std::vector<Vec> all;
+    for (int k = 0; k < I; ++k) all.push_back({se[k], 0, k});
+    for (int k = 0; k < I; ++k) all.push_back({so[k], 1, k});
+    std::stable_sort(all.begin(), all.end(), [](const Vec &a, const Vec &b) { return a.sigma > b.sigma; });
+    auto sorted_block = [](std::vector<double> s, int keep) {
+        std::sort(s.begin(), s.end(), std::greater<double>());
+        s.resize(std::min<size_t>(s.size(), keep));
+        return s;
+    };
+    plan->s_even = sorted_block(se, std::min(I, nE));
+    plan->s_odd = sorted_block(so, std::min(I, nO));
+
+    // K: requested, or the smallest K holding `energy` of sum(s^2) (Sec. 4 leaves
+    // K to the user), extended over singular values tied with the K-th.
+    double tot = 0;
+    for (auto &v : all) tot += v.sigma * v.sigma;
+    int n_all = (int)all.size();
+    int K = K_req;
+    if (K <= 0) {
+        double acc = 0;
+        K = n_all;
+        for (int k = 0; k < n_all; ++k) {
+            acc += all[k].sigma * all[k].sigma;
+            if (acc >= energy * tot) {
+                K = k + 1;
+                break;
+            }
+        }
+        while (K < n_all && all[K - 1].sigma - all[K].sigma <= 1e-12 * all[K - 1].sigma) ++K;
+    }
+    if (K > n_all) return fail(FCC_ERR_INVALID_ARG, "K exceeds the number of singular values");
+    if (all[K - 1].sigma <= 1e-12 * all[0].sigma)
+        return fail(FCC_ERR_INVALID_ARG, "K exceeds the numerical rank of W");
+
+    std::vector<const Vec *> ev, ov;
+    for (int k = 0; k < K; ++k) (all[k].parity == 0 ? ev : ov).push_back(&all[k]);
+    const int KE = (int)ev.size(), KO = (int)ov.size();
+    in.K = K;
+    in.K_even = KE;
+    in.K_odd = KO;
+    plan->Pe.assign((size_t)KE * nE, 0.0);
+    plan->Po.assign((size_t)KO * nO, 0.0);
+    plan->Ue.assign((size_t)I * KE, 0.0);
+    plan->Uo.assign((size_t)I * KO, 0.0);
+    const double r2 = std::sqrt(2.0);
+    // For each kept vector: sigma v = y (the rotated row), u = J row.  Canonical
+    // sign: the largest-magnitude entry of v (lowest index on ties) is positive.
+    auto emit = [&](const Vec *v, const std::vector<double> &X, const std::vector<double> &Jm,
+                    int len, int col, int K_par, std::vector<double> &Pm, std::vector<double> &Um,
+                    bool even) {
+        const double *y = &X[(size_t)v->idx * len];
+        const double *u = &Jm[(size_t)v->idx * I];
+        int am = 0;
+        for (int t = 1; t < len; ++t)
+            if (std::fabs(y[t]) > std::fabs(y[am])) am = t;
+        double sg = y[am] < 0 ? -1.0 : 1.0;
+        for (int t = 0; t < len; ++t) {
+            double w = even ? (t < Q ? r2 : 1.0) : r2;
+            Pm[(size_t)col * len + t] = sg * y[t] / w;
+        }
+        for (int i = 0; i < I; ++i) Um[(size_t)i * K_par + col] = sg * u[i];
+    };
+    for (int k = 0; k < KE; ++k) emit(ev[k], Xe, Je, nE, k, KE, plan->Pe, plan->Ue, true);
+    for (int k = 0; k < KO; ++k) emit(ov[k], Xo, Jo, nO, k, KO, plan->Po, plan->Uo, false);
+    return FCC_OK;
+}
+
+}  // namespace fcc

@@ -1,0 +1,55 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads and
+exports every function include/fcc.h declares, and the binding agrees."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2204_13622_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "fcc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fcc_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_lists_every_binding_export():
+    from paper_2204_13622_gb300 import binding
+    assert declared_functions() == sorted(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    from paper_2204_13622_gb300 import binding
+    for code in binding.STATUS:
+        s = lib.fcc_status_string(code).decode()
+        assert s and s != "unknown status"
+    assert lib.fcc_status_string(99).decode() == "unknown status"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    from paper_2204_13622_gb300 import binding
+    assert lib.fcc_plan_create(None, None) == 1
+    assert lib.fcc_tdoa(None, None, 0, None, None, None, None, None, None) == 1
+    assert lib.fcc_plan_info(None, None) == 1
+    lib.fcc_plan_destroy(None)  # no-op
+    d = binding.PlanDesc(1, None, 16000.0, 512, 343.0, 3.0, 4, 0, 0.999, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.fcc_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1  # n_mics < 2
+    d = binding.PlanDesc(4, None, 16000.0, 500, 343.0, 3.0, 4, 0, 0.999, 0, 0)
+    assert lib.fcc_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1  # N not a power of two
+    assert "power of two" in lib.fcc_last_error().decode()
