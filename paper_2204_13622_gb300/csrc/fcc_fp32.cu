@@ -36,7 +36,12 @@
 namespace fcc {
 namespace {
 
-constexpr int kMaxComputeWarps = 8;
+
+// Registers are split per SM sub-partition (16K each, warps assigned round
+// robin), so the register cap and the warp count must fit together:
+// KH = 8 keeps up to 224 registers with at most 8 warps (7 compute + producer);
+// smaller KH cap registers at 168 and allow 8 compute warps + producer.
+__host__ __device__ constexpr int max_compute_warps(int kh) { return kh == 8 ? 7 : 8; }
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -108,11 +113,11 @@ __device__ __forceinline__ float2 unit_phase(float2 x, bool &bad)
         float r = rsqrtf(s);
         return make_float2(x.x * r, x.y * r);
     }
-    float m = fmaxf(fabsf(x.x), fabsf(x.y));
-    if (!(m <= FLT_MAX)) {  // NaN or Inf
+    if (!(fabsf(x.x) <= FLT_MAX) || !(fabsf(x.y) <= FLT_MAX)) {  // NaN or Inf
         bad = true;
         return make_float2(0.f, 0.f);
     }
+    float m = fmaxf(fabsf(x.x), fabsf(x.y));
     if (m == 0.f) return make_float2(0.f, 0.f);
     float a = x.x / m, b = x.y / m;
     float r = rsqrtf(fmaf(a, a, b * b));
@@ -173,7 +178,7 @@ __device__ __forceinline__ float y_at(const float *__restrict__ recon, int cente
 }
 
 template <int KH>
-__global__ void __maxnreg__(224) fcc_fp32_kernel(const Fp32Params p)
+__global__ void __maxnreg__(KH == 8 ? 224 : 168) fcc_fp32_kernel(const Fp32Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const SmemLayout lay = smem_layout(p.S, p.n_slots, p.Q, KH, p.F, p.frame_floats * 4);
@@ -502,10 +507,10 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan)
     double best_score = -1.0;
     for (int C = 4; C <= 16 && C <= in.Q; C <<= 1) {
         const int lanes = n_slots * C;
-        for (int GW = 1; GW <= kMaxComputeWarps; GW <<= 1) {
+        for (int GW = 1; GW <= max_compute_warps(kh); GW <<= 1) {
             if (lanes > GW * 32) continue;
             const int F = (GW * 32) / lanes;
-            for (int G = kMaxComputeWarps / GW; G >= 1; --G) {
+            for (int G = max_compute_warps(kh) / GW; G >= 1; --G) {
                 if (want_g && G != want_g) continue;
                 for (int Sg = 3; Sg >= 1; --Sg) {
                     if (want_sg && Sg != want_sg) continue;

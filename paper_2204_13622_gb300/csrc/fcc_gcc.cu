@@ -34,8 +34,9 @@ __device__ __forceinline__ float2 unit(float2 x)
         float r = rsqrtf(s);
         return make_float2(x.x * r, x.y * r);
     }
+    if (!(fabsf(x.x) <= FLT_MAX) || !(fabsf(x.y) <= FLT_MAX)) return make_float2(0.f, 0.f);
     float m = fmaxf(fabsf(x.x), fabsf(x.y));
-    if (!(m <= FLT_MAX) || m == 0.f) return make_float2(0.f, 0.f);
+    if (m == 0.f) return make_float2(0.f, 0.f);
     float a = x.x / m, b = x.y / m;
     float r = rsqrtf(fmaf(a, a, b * b));
     return make_float2(a * r, b * r);

@@ -84,7 +84,7 @@ def stft(x: np.ndarray, N: int, hop: int) -> np.ndarray:
     win = 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(N) / N)
     idx = np.arange(T)[:, None] * hop + np.arange(N)[None, :]
     frames = x[:, idx] * win  # [n_ch, T, N]
-    return np.fft.rfft(frames, axis=-1).transpose(1, 0, 2)
+    return np.ascontiguousarray(np.fft.rfft(frames, axis=-1).transpose(1, 0, 2))
 
 
 @dataclass
