@@ -184,6 +184,42 @@ fcc_status_t fcc_gcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, 
                           float *d_peak, float *d_corr, void *stream);
 
 /*
+ * Basis construction that allocates no device memory.  The paper has no
+ * counterpart: it builds its bases once, offline.
+ *
+ * Who needs it: callers that must not call cudaMalloc / cudaFree while they
+ * run -- a real-time audio process whose other streams must never stall (both
+ * calls may synchronise the whole device), code embedded in a framework that
+ * owns every device byte through its own pool, or an array whose geometry
+ * changes on the fly and must get fresh bases without touching the allocator.
+ *
+ * It computes exactly what fcc_plan_create's basis step computes (the even
+ * and odd halves of W in FP64, a Jacobi SVD of each on the GPU, the K rule,
+ * canonical signs) for the sizes `desc` describes, but the working matrices
+ * live in one static device array of 4 MiB inside the library, which every GPU
+ * that loads the library keeps until the process exits.  The grid must satisfy
+ * I (N/2 + 1) + 2 I^2 + 32 <= 524288 doubles (I = 2 L lag_den + 1); larger
+ * grids return FCC_ERR_UNSUPPORTED with the sizes in fcc_last_error().  No
+ * other allocation is made on the device.
+ *
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call uses the same array, so
+ * calls whose work overlaps on the GPU (from several threads or streams) race
+ * and must be serialised by the caller.  Kernels and copies run on `stream`;
+ * the call returns after synchronising it.
+ *
+ * Outputs are host arrays (each may be NULL), laid out as in
+ * fcc_plan_singular_values / fcc_plan_bases: s_even[min(I, Q+1)],
+ * s_odd[min(I, Q)], Pe[K_even][Q+1], Po[K_odd][Q], Ue[I][K_even],
+ * Uo[I][K_odd].  K is known only after the SVD: call once with only `info`
+ * to learn K_even / K_odd, then again with arrays of those sizes.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, NOT_CONVERGED.
+ */
+fcc_status_t fcc_plan_bases_noalloc(const fcc_plan_desc_t *desc, fcc_plan_info_t *info,
+                                    double *s_even, double *s_odd, double *Pe, double *Po,
+                                    double *Ue, double *Uo, void *stream);
+
+/*
  * Synchronise `stream` (NULL = legacy default), then read and clear the plan's
  * device error word: FCC_OK, FCC_ERR_NONFINITE or FCC_ERR_TIMEOUT.
  */

@@ -23,7 +23,7 @@ PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 # every symbol include/fcc.h declares
 EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_taus",
            "fcc_plan_singular_values", "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa",
-           "fcc_plan_sync", "fcc_status_string", "fcc_last_error"]
+           "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -71,12 +71,15 @@ def lib():
         L.fcc_tdoa_host.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
         L.fcc_gcc_tdoa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
         L.fcc_plan_sync.argtypes = [_vp, _vp]
+        L.fcc_plan_bases_noalloc.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(PlanInfo), _dp, _dp,
+                                             _dp, _dp, _dp, _dp, _vp]
         L.fcc_status_string.argtypes = [ctypes.c_int]
         L.fcc_status_string.restype = ctypes.c_char_p
         L.fcc_last_error.argtypes = []
         L.fcc_last_error.restype = ctypes.c_char_p
         for name in ("fcc_plan_create", "fcc_plan_info", "fcc_plan_taus", "fcc_plan_singular_values",
-                     "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa", "fcc_plan_sync"):
+                     "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa", "fcc_plan_sync",
+                     "fcc_plan_bases_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -223,3 +226,27 @@ class Plan:
     def sync(self, stream=None):
         """Synchronise and raise if a kernel latched an error (NaN/Inf input, timeout)."""
         check(lib().fcc_plan_sync(self._h, _stream(stream, self.device)), "fcc_plan_sync")
+
+
+def plan_bases_noalloc(n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0, mic_xyz=None,
+                       c: float = 343.0, K: int = 0, energy: float = 0.999, device: int = 0, stream=None):
+    """fcc_plan_bases_noalloc: the plan's bases built in the library's static
+    device scratch (no device allocation).  Returns (info dict, s_even, s_odd,
+    Pe, Po, Ue, Uo) as numpy arrays."""
+    xyz = None
+    if mic_xyz is not None:
+        xyz = np.ascontiguousarray(mic_xyz, np.float64).reshape(n_mics, 3)
+    desc = PlanDesc(n_mics, xyz.ctypes.data_as(_dp) if xyz is not None else None, float(fs), int(N),
+                    float(c), float(tau_max), int(lag_den), int(K), float(energy), 0, int(device))
+    st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    info = PlanInfo()
+    check(lib().fcc_plan_bases_noalloc(ctypes.byref(desc), ctypes.byref(info), None, None, None, None, None,
+                                       None, st), "fcc_plan_bases_noalloc")
+    I, Q, KE, KO = info.I, info.Q, info.K_even, info.K_odd
+    se, so = np.empty(min(I, Q + 1)), np.empty(min(I, Q))
+    Pe, Po, Ue, Uo = np.empty((KE, Q + 1)), np.empty((KO, Q)), np.empty((I, KE)), np.empty((I, KO))
+    check(lib().fcc_plan_bases_noalloc(ctypes.byref(desc), ctypes.byref(info), se.ctypes.data_as(_dp),
+                                       so.ctypes.data_as(_dp), Pe.ctypes.data_as(_dp), Po.ctypes.data_as(_dp),
+                                       Ue.ctypes.data_as(_dp), Uo.ctypes.data_as(_dp), st),
+          "fcc_plan_bases_noalloc")
+    return {k: getattr(info, k) for k, _ in PlanInfo._fields_}, se, so, Pe, Po, Ue, Uo

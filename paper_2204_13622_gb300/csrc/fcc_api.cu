@@ -25,26 +25,6 @@ fcc_status_t cuda_fail(cudaError_t e, const char *what)
 
 namespace {
 
-// Makes `dev` current for the scope of one entry point and restores the
-// caller's device afterwards.
-struct DeviceScope {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceScope(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceScope()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 int pair_index(int M, int i, int j) { return i * M - i * (i + 1) / 2 + (j - i - 1); }
 
 // Tile the pair triangle into 2x2 blocks of microphone groups {2a, 2a+1}:
@@ -143,32 +123,10 @@ void free_plan(fcc_plan *p)
 }  // namespace
 }  // namespace fcc
 
-using namespace fcc;
-
-extern "C" {
-
-const char *fcc_status_string(fcc_status_t s)
+// Validate a plan description and derive the plan's sizes (host only).
+fcc_status_t fcc::plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t &in, int &dev)
 {
-    switch (s) {
-    case FCC_OK: return "ok";
-    case FCC_ERR_INVALID_ARG: return "invalid argument";
-    case FCC_ERR_UNSUPPORTED: return "unsupported";
-    case FCC_ERR_OOM: return "out of memory";
-    case FCC_ERR_CUDA: return "CUDA error";
-    case FCC_ERR_TIMEOUT: return "device wait timed out";
-    case FCC_ERR_NONFINITE: return "non-finite input";
-    case FCC_ERR_NOT_CONVERGED: return "SVD did not converge";
-    }
-    return "unknown status";
-}
-
-const char *fcc_last_error(void) { return g_last_error.c_str(); }
-
-fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
-{
-    g_last_error.clear();
-    if (!d || !out) return fail(FCC_ERR_INVALID_ARG, "null desc or out");
-    *out = nullptr;
+    if (!d) return fail(FCC_ERR_INVALID_ARG, "null desc");
     if (d->n_mics < 2) return fail(FCC_ERR_INVALID_ARG, "n_mics < 2");
     if (d->n_mics > 16) return fail(FCC_ERR_UNSUPPORTED, "n_mics > 16");
     if (!(d->fs > 0)) return fail(FCC_ERR_INVALID_ARG, "fs <= 0");
@@ -201,14 +159,9 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
     if (I > 1025) return fail(FCC_ERR_UNSUPPORTED, "more than 1025 lag candidates");
     if (L * 2 > d->N / 2) return fail(FCC_ERR_INVALID_ARG, "lag range too large for N");
 
-    int dev = d->device;
+    dev = d->device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(FCC_ERR_CUDA, "no CUDA device");
-    DeviceScope scope(dev);
-    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
-    fcc_plan *p = new (std::nothrow) fcc_plan();
-    if (!p) return fail(FCC_ERR_OOM, "host allocation");
-    p->device = dev;
-    fcc_plan_info_t &in = p->info;
+    in = fcc_plan_info_t{};
     in.M = d->n_mics;
     in.P = in.M * (in.M - 1) / 2;
     in.N = d->N;
@@ -222,8 +175,48 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
     in.delta = 1.0 / d->lag_den;
     in.fs = d->fs;
     in.c = c;
-    p->taus.resize(I);
-    for (int i = 0; i < I; ++i) p->taus[i] = (double)(i - in.center) / (double)in.den;
+    return FCC_OK;
+}
+
+using namespace fcc;
+
+extern "C" {
+
+const char *fcc_status_string(fcc_status_t s)
+{
+    switch (s) {
+    case FCC_OK: return "ok";
+    case FCC_ERR_INVALID_ARG: return "invalid argument";
+    case FCC_ERR_UNSUPPORTED: return "unsupported";
+    case FCC_ERR_OOM: return "out of memory";
+    case FCC_ERR_CUDA: return "CUDA error";
+    case FCC_ERR_TIMEOUT: return "device wait timed out";
+    case FCC_ERR_NONFINITE: return "non-finite input";
+    case FCC_ERR_NOT_CONVERGED: return "SVD did not converge";
+    }
+    return "unknown status";
+}
+
+const char *fcc_last_error(void) { return g_last_error.c_str(); }
+
+fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
+{
+    g_last_error.clear();
+    if (!d || !out) return fail(FCC_ERR_INVALID_ARG, "null desc or out");
+    *out = nullptr;
+    fcc_plan_info_t info0;
+    int dev = 0;
+    fcc_status_t st0 = plan_info_from_desc(d, info0, dev);
+    if (st0 != FCC_OK) return st0;
+    DeviceScope scope(dev);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    fcc_plan *p = new (std::nothrow) fcc_plan();
+    if (!p) return fail(FCC_ERR_OOM, "host allocation");
+    p->device = dev;
+    p->info = info0;
+    fcc_plan_info_t &in = p->info;
+    p->taus.resize(in.I);
+    for (int i = 0; i < in.I; ++i) p->taus[i] = (double)(i - in.center) / (double)in.den;
     cudaError_t e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         free_plan(p);

@@ -20,6 +20,26 @@ enum : unsigned {
 fcc_status_t fail(fcc_status_t st, const std::string &msg);
 fcc_status_t cuda_fail(cudaError_t e, const char *what);
 
+// Makes `dev` current for the scope of one entry point and restores the
+// caller's device afterwards.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 #define FCC_CUDA_TRY(call)                                          \
     do {                                                            \
         cudaError_t e__ = (call);                                   \
@@ -99,7 +119,11 @@ struct fcc_plan {
 };
 
 namespace fcc {
+fcc_status_t plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t &in, int &dev);
 fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy);
+fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, const std::vector<double> &Xo,
+                               const std::vector<double> &Je, const std::vector<double> &Jo, int K_req,
+                               double energy);
 fcc_status_t choose_fp32_geometry(fcc_plan *plan);
 fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,
                          float *peak, float *tau, float *coef, float *corr, cudaStream_t st);

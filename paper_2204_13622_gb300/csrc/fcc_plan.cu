@@ -18,6 +18,7 @@
 // dictionary for the kernels.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 
 #include "fcc_internal.h"
@@ -63,10 +64,10 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // One-sided Jacobi on the n row vectors x_k (length len) of X [n][len]:
 // rotations x_p <- c x_p - s x_q, x_q <- s x_p + c x_q make the rows mutually
-// orthogonal; the same rotations applied to J (identity at start, row k holding
-// column k of the accumulated orthogonal matrix) give X_0^T J^T... i.e. with
-// A = X_0 (I x len), A = J^T-columns * Y: A = sum_k J[k][:]^T y_k^T.
-// Block b of the grid works on matrix b.
+// orthogonal.  The same rotations are applied to the rows of J (identity at
+// the start), so at convergence X = J A with J orthogonal and rows y_k of X
+// orthogonal; hence A = J^T X = sum_k J[k][:]^T y_k, i.e. u_k = J[k][:],
+// sigma_k = |y_k| and v_k = y_k / sigma_k.  Block b of the grid works on job b.
 struct JacobiJob {
     double *X;
     double *J;
@@ -145,6 +146,20 @@ struct Vec {
     int idx;     // row within its block
 };
 
+// Build the two halves of W and run the Jacobi SVD of each (one CTA per half).
+void launch_basis_kernels(const fcc_plan_info_t &in, double *d_Ae, double *d_Ao, double *d_Je, double *d_Jo,
+                          int *d_sw, cudaStream_t st)
+{
+    const int I = in.I, Q = in.Q;
+    dim3 gb((Q + 1 + 127) / 128, I);
+    build_halves_kernel<<<gb, 128, 0, st>>>(I, in.L * in.den, in.den, in.N, Q, d_Ae, d_Ao);
+    // ||A||_F^2 = I (N/2 + 1) per block at most; vectors below 1e-30 of it are noise
+    double tiny2 = 1e-30 * (double)I * (double)(in.N / 2 + 1);
+    JacobiJob je{d_Ae, d_Je, I, Q + 1, d_sw};
+    JacobiJob jo{d_Ao, d_Jo, I, Q, d_sw + 1};
+    jacobi_svd_kernel<<<2, kJacobiThreads, 0, st>>>(je, jo, tiny2);
+}
+
 }  // namespace
 
 fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
@@ -170,13 +185,7 @@ fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
         (void)cudaGetLastError();
         return fail(FCC_ERR_OOM, "plan workspace (" + std::to_string(bytes) + " bytes)");
     }
-    dim3 gb((nE + 127) / 128, I);
-    build_halves_kernel<<<gb, 128>>>(I, in.L * in.den, in.den, in.N, Q, d_Ae, d_Ao);
-    // ||A||_F^2 = I (N/2 + 1) per block at most; vectors below 1e-30 of it are noise
-    double tiny2 = 1e-30 * (double)I * (double)(in.N / 2 + 1);
-    JacobiJob je{d_Ae, d_Je, I, nE, d_sw};
-    JacobiJob jo{d_Ao, d_Jo, I, nO, d_sw + 1};
-    jacobi_svd_kernel<<<2, kJacobiThreads>>>(je, jo, tiny2);
+    launch_basis_kernels(in, d_Ae, d_Ao, d_Je, d_Jo, d_sw, 0);
     std::vector<double> Xe((size_t)I * nE), Xo((size_t)I * nO), Je((size_t)I * I), Jo((size_t)I * I);
     int sw[2] = {0, 0};
     cudaError_t e = cudaGetLastError();
@@ -188,6 +197,18 @@ fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "plan basis construction");
     if (sw[0] < 0 || sw[1] < 0) return fail(FCC_ERR_NOT_CONVERGED, "Jacobi SVD did not converge");
+    return finish_plan_bases(plan, Xe, Xo, Je, Jo, K_req, energy);
+}
+
+// Host part of the basis construction, from the rotated rows (sigma v) and the
+// accumulated rotations (u) of both halves: merge the singular values, pick K,
+// fix signs and write the cropped bases and the dictionary into the plan.
+fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, const std::vector<double> &Xo,
+                               const std::vector<double> &Je, const std::vector<double> &Jo, int K_req,
+                               double energy)
+{
+    fcc_plan_info_t &in = plan->info;
+    const int I = in.I, Q = in.Q, nE = Q + 1, nO = Q;
 
     // singular values = row norms of the rotated matrices
     auto norms = [](const std::vector<double> &X, int n, int len) {
@@ -267,4 +288,92 @@ fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
     return FCC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free basis construction (fcc_plan_bases_noalloc).  The working
+// matrices of the two Jacobi SVDs live in one static device array instead of
+// cudaMalloc'd memory.  Layout (doubles): [0, 32) two int sweep counters,
+// then A_e [I][Q+1], A_o [I][Q], J_e [I][I], J_o [I][I].
 }  // namespace fcc
+
+// 4 MiB, held by every GPU that loads this library until the process exits.
+static constexpr size_t kNoAllocDoubles = size_t(1) << 19;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace fcc {
+namespace {
+
+constexpr size_t kNoAllocHeader = 32;  // 256 bytes
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[256] = {};
+
+// Device address of the static array on the current device (looked up once
+// per device; the host-side symbol is not a device address).
+fcc_status_t noalloc_scratch(int dev, double **out)
+{
+    if (dev < 0 || dev >= 256) return fail(FCC_ERR_UNSUPPORTED, "device ordinal above 255");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return FCC_OK;
+}
+
+}  // namespace
+}  // namespace fcc
+
+extern "C" fcc_status_t fcc_plan_bases_noalloc(const fcc_plan_desc_t *desc, fcc_plan_info_t *info,
+                                               double *s_even, double *s_odd, double *Pe, double *Po,
+                                               double *Ue, double *Uo, void *stream)
+{
+    using namespace fcc;
+    fcc_plan tmp;  // host-side fields only; nothing on the device is created
+    int dev = 0;
+    fcc_status_t st = plan_info_from_desc(desc, tmp.info, dev);
+    if (st != FCC_OK) return st;
+    const fcc_plan_info_t &in = tmp.info;
+    const size_t I = in.I, Q = in.Q;
+    const size_t need = kNoAllocHeader + I * (2 * Q + 1) + 2 * I * I;
+    if (need > kNoAllocDoubles)
+        return fail(FCC_ERR_UNSUPPORTED,
+                    "grid needs " + std::to_string(need * 8) + " bytes of scratch; the static array holds " +
+                        std::to_string(kNoAllocDoubles * 8) + " (I (N/2 + 1) + 2 I^2 + 32 <= 524288 doubles)");
+    DeviceScope scope(dev);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    double *base = nullptr;
+    st = noalloc_scratch(dev, &base);
+    if (st != FCC_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    int *d_sw = reinterpret_cast<int *>(base);
+    double *d_Ae = base + kNoAllocHeader;
+    double *d_Ao = d_Ae + I * (Q + 1);
+    double *d_Je = d_Ao + I * Q;
+    double *d_Jo = d_Je + I * I;
+    // the sweep counters start at -1 ("not converged"), so stale contents of a
+    // previous call can never pass for this call's result
+    FCC_CUDA_TRY(cudaMemsetAsync(d_sw, 0xff, 2 * sizeof(int), cs));
+    launch_basis_kernels(in, d_Ae, d_Ao, d_Je, d_Jo, d_sw, cs);
+    FCC_CUDA_TRY(cudaGetLastError());
+    std::vector<double> Xe(I * (Q + 1)), Xo(I * Q), Je(I * I), Jo(I * I);
+    int sw[2] = {-1, -1};
+    FCC_CUDA_TRY(cudaMemcpyAsync(Xe.data(), d_Ae, sizeof(double) * Xe.size(), cudaMemcpyDeviceToHost, cs));
+    FCC_CUDA_TRY(cudaMemcpyAsync(Xo.data(), d_Ao, sizeof(double) * Xo.size(), cudaMemcpyDeviceToHost, cs));
+    FCC_CUDA_TRY(cudaMemcpyAsync(Je.data(), d_Je, sizeof(double) * Je.size(), cudaMemcpyDeviceToHost, cs));
+    FCC_CUDA_TRY(cudaMemcpyAsync(Jo.data(), d_Jo, sizeof(double) * Jo.size(), cudaMemcpyDeviceToHost, cs));
+    FCC_CUDA_TRY(cudaMemcpyAsync(sw, d_sw, sizeof(sw), cudaMemcpyDeviceToHost, cs));
+    FCC_CUDA_TRY(cudaStreamSynchronize(cs));
+    if (sw[0] < 0 || sw[1] < 0) return fail(FCC_ERR_NOT_CONVERGED, "Jacobi SVD did not converge");
+    st = finish_plan_bases(&tmp, Xe, Xo, Je, Jo, desc->K, desc->energy > 0 ? desc->energy : 0.999);
+    if (st != FCC_OK) return st;
+    if (info) *info = tmp.info;
+    if (s_even) std::copy(tmp.s_even.begin(), tmp.s_even.end(), s_even);
+    if (s_odd) std::copy(tmp.s_odd.begin(), tmp.s_odd.end(), s_odd);
+    if (Pe) std::copy(tmp.Pe.begin(), tmp.Pe.end(), Pe);
+    if (Po) std::copy(tmp.Po.begin(), tmp.Po.end(), Po);
+    if (Ue) std::copy(tmp.Ue.begin(), tmp.Ue.end(), Ue);
+    if (Uo) std::copy(tmp.Uo.begin(), tmp.Uo.end(), Uo);
+    return FCC_OK;
+}
