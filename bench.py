@@ -19,10 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
-
-import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -75,6 +72,7 @@ def rank_seed(rank: int) -> int:
 # clocks
 # ----------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi sampling (every 100 ms) while the timed region runs."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -82,39 +80,49 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.rows = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([c.strip() for c in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self.proc = None
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # first sample before the timed work starts
+        except Exception:
+            self.proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self.proc is None:
+            return
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            cols = [c.strip() for c in line.split(",")]
+            if len(cols) == 9:
+                self.rows.append(cols)
 
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in self.rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in self.rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in self.rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(self.rows)}
 
 
 # ----------------------------------------------------------------------------
@@ -148,7 +156,8 @@ def run_reference(args, rank, world):
     w = workloads.CIRCLE8
     if rank != 0:
         return None
-    budget = float(os.environ.get("FCC_REF_STEP_SECONDS", "8"))
+    # each step is a bounded sample sized so the whole run stays near 1.5 minutes
+    budget = float(os.environ.get("FCC_REF_STEP_SECONDS", str(max(0.5, min(8.0, 90.0 / max(1, args.steps))))))
     sample = {}
 
     def gen(n):
@@ -185,9 +194,9 @@ def run_fcc(args, rank, world, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
-    X = w.spectra(device=dev, seed=rank_seed(rank))
+    T, P = (args.frames or w.T), w.P
+    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
     plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local)
-    T, P = w.T, w.P
     out = plan.tdoa(X, tau_hat=True)  # allocates the outputs once
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 3)):
@@ -217,6 +226,15 @@ def run_fcc(args, rank, world, local):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    if args.only == "fcc":
+        res = None
+        if rank == 0:
+            res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                   "warmup": args.warmup, "ms_per_step": ms_max, "config": {"workload": w.name, "frames": T},
+                   "note": "FCC kernel only (profiling run)", "roofline_achieved_gbs": achieved}
+        plan.close()
+        return res
 
     # ---- same-GPU GCC-PHAT baseline on the same frames
     gout = plan.gcc_tdoa(X)
@@ -264,7 +282,8 @@ def run_fcc(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "frames": T, "mics": w.M, "pairs": P, "N": w.N,
+            "config": {"workload": w.name if T == w.T else f"{w.name} truncated to {T} frames",
+                       "frames": T, "mics": w.M, "pairs": P, "N": w.N,
                        "lag_grid": f"[-{w.L}, {w.L}] step 1/{w.lag_den} (I={plan.I})",
                        "K": plan.K, "K_even": plan.K_even, "K_odd": plan.K_odd,
                        "outputs": "lag_idx, peak, tau_hat",
@@ -290,9 +309,11 @@ def run_fcc(args, rank, world, local):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcc", choices=["fcc", "reference"])
+    ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
+    ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -65,21 +65,28 @@ std::vector<Slot> make_slots(int M)
     return out;
 }
 
-// FP32 tables for the kernel:
-//   basis [Q+1][2 kh]: row f = (Pe[0..KE)(f), 0.., Po[0..KO)(f), 0..), Po(Q) = 0;
-//   recon [center+1][4][kh]: for tau = m/den >= 0, a = cos(pi tau/2), b = sin(pi tau/2),
-//     gSe = 2a Ue(tau), gSo = -2b Uo(tau), gDe = 2b Ue(tau), gDo = 2a Uo(tau), so that
-//     y(+tau) = S - D and y(-tau) = S + D with S = gSe.Re z_e + gSo.Re z_o and
-//     D = gDe.Im z_e + gDo.Im z_o (Ue even and Uo odd in tau).
+// FP32 tables for the kernel (kh = bases per parity, padded with zeros):
+//   basis: rows of BS floats, (pe_0 .. pe_{kh-1}, po_0 .. po_{kh-1}, pad); chunk c of
+//     the bin-pair axis (QC = Q / C rows) starts at row c (QC + 1) -- one zero row
+//     between chunks staggers their shared-memory banks -- and bin N/4 (no odd
+//     part) is row C (QC + 1);
+//   recon [center+1][4 kh]: row m (tau = m/den >= 0), per k the four weights
+//     (gSe, gDe, gSo, gDo) = (2a Ue, 2b Ue, -2b Uo, 2a Uo) at tau, with
+//     a = cos(pi tau / 2), b = sin(pi tau / 2); then y(+tau) = S - D and
+//     y(-tau) = S + D where S = gSe.Re z_e + gSo.Re z_o and D = gDe.Im z_e + gDo.Im z_o
+//     (Ue is even and Uo odd in tau).
 void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<float> &recon)
 {
     const fcc_plan_info_t &in = plan->info;
     const int kh = plan->kh, Q = in.Q, KE = in.K_even, KO = in.K_odd;
-    basis.assign((size_t)(Q + 1) * 2 * kh, 0.f);
+    const int C = plan->geo.C, BS = plan->geo.BS, QC = Q / C;
+    basis.assign((size_t)(Q + C + 1) * BS, 0.f);
     for (int f = 0; f <= Q; ++f) {
-        for (int k = 0; k < KE; ++k) basis[(size_t)f * 2 * kh + k] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
+        const int row = f < Q ? (f / QC) * (QC + 1) + f % QC : C * (QC + 1);
+        float *r = &basis[(size_t)row * BS];
+        for (int k = 0; k < KE; ++k) r[k] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
         if (f < Q)
-            for (int k = 0; k < KO; ++k) basis[(size_t)f * 2 * kh + kh + k] = (float)plan->Po[(size_t)k * Q + f];
+            for (int k = 0; k < KO; ++k) r[kh + k] = (float)plan->Po[(size_t)k * Q + f];
     }
     recon.assign((size_t)(in.center + 1) * 4 * kh, 0.f);
     for (int m = 0; m <= in.center; ++m) {
@@ -89,13 +96,13 @@ void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<fl
         float *g = &recon[(size_t)m * 4 * kh];
         for (int k = 0; k < KE; ++k) {
             const double u = plan->Ue[(size_t)i * KE + k];
-            g[k] = (float)(2.0 * a * u);
-            g[2 * kh + k] = (float)(2.0 * b * u);
+            g[4 * k] = (float)(2.0 * a * u);
+            g[4 * k + 1] = (float)(2.0 * b * u);
         }
         for (int k = 0; k < KO; ++k) {
             const double u = plan->Uo[(size_t)i * KO + k];
-            g[kh + k] = (float)(-2.0 * b * u);
-            g[3 * kh + k] = (float)(2.0 * a * u);
+            g[4 * k + 2] = (float)(-2.0 * b * u);
+            g[4 * k + 3] = (float)(2.0 * a * u);
         }
     }
 }
@@ -238,7 +245,8 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
             return st;
         }
         std::vector<float> basis, recon;
-        pack_tables(p, basis, recon);
+        if (p->geo.C) pack_tables(p, basis, recon);
+        else basis.assign(4, 0.f), recon.assign(4, 0.f);  // N > 1024: no FP32 kernel
         e = cudaMalloc(&p->d_basis, basis.size() * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(&p->d_recon, recon.size() * sizeof(float));
         if (e == cudaSuccess) e = cudaMemcpy(p->d_basis, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice);

@@ -1,30 +1,35 @@
 // fcc_fp32.cu -- the FP32 FCC hot path for sm_103a.
 //
-// One persistent kernel does, per frame tile:
-//   1. stage   : a warp-specialised producer copies whole frame tiles of spectra
-//                (contiguous [F][M][B] complex64) into a ring of shared-memory
-//                stages with one cp.async.bulk per tile, completed on an mbarrier
-//                (bounded waits everywhere; no multicast);
-//   2. PHAT    : the consumer group normalises each bin of each microphone in
-//                place, u = X / |X| (0 for |X| = 0).  Because
-//                X_i X_j^* / |X_i X_j^*| = u_i u_j^*, this is the phase transform
-//                of Sec. 2 (eq. 1 with alpha = 1) for every pair at M (not P)
-//                reciprocal square roots per bin;
-//   3. fold +
-//      project: each lane owns a 2x2 block of the pair triangle (mics {i1,i2} x
-//                {j1,j2}, 4 pairs sharing 4 microphone rows) and one chunk of the
-//                frequency axis; per bin pair (f, N/2-f) it forms the four cross
-//                spectra in registers, folds them into x_s / x_d (Eq. 8) and
-//                accumulates the real and imaginary parts against the cropped
-//                even and odd bases (Eqs. 7, 9).  No pair spectrum leaves
-//                registers;
-//   4. reduce  : the chunk lanes of a slot combine their partial projections
-//                with a reduce-scatter over warp shuffles, so lane q ends up
-//                holding the 2K coefficients of pair q of the block;
-//   5. output  : y(tau) on the lag grid from the 2K coefficients (using the
-//                grid's symmetry, one pass over tau >= 0 yields y(tau) and
-//                y(-tau)), argmax with the lowest index winning ties, the peak,
-//                and (optionally) the FP64 three-point quadratic refinement.
+// One persistent kernel.  A CTA holds G groups of GW warps; every group owns S/G
+// stages of a shared-memory ring and streams its own frame tiles through them
+// (tile k of the CTA belongs to group k % G and lives in stage k % S):
+//   1. stage    : one cp.async.bulk per tile (F whole frames, contiguous
+//                 [F][M][B] complex64), completed on the stage's mbarrier.  The
+//                 group issues the copy of its next tile into a stage as soon as
+//                 its own main loop has left it, so the copy overlaps the
+//                 group's reduction and reconstruction.  All waits are bounded.
+//   2. PHAT +   : each microphone row is normalised, u = X / |X| (0 for X = 0)
+//      re-lay     (Sec. 2, eq. 1 with alpha = 1: X_i X_j^* / |X_i X_j^*| =
+//                 u_i u_j^*, so M instead of P reciprocal square roots per bin),
+//                 and rewritten in place in "folded" order: the 16-byte record fp
+//                 holds (u(fp), u(N/2 - fp)) for fp < N/4 -- the two bins that
+//                 Eq. 8 adds and subtracts -- and the lone bin N/4 sits at one
+//                 end of the row.  Rows at odd positions are shifted by 8 bytes
+//                 so that every record is 16-byte aligned while each row stays
+//                 inside its own bytes (N/2 + 1 is odd).
+//   3. fold +   : a lane owns a 2x2 block of the pair triangle (mics {i1,i2} x
+//      project    {j1,j2}: 4 pairs from 4 rows) and one chunk of the bin-pair
+//                 axis.  Per record it forms the 4 x 2 cross spectra in
+//                 registers, folds them into x_s / x_d (Eq. 8) with packed FP32
+//                 adds, and accumulates (Re, Im) x_s against the even cropped
+//                 bases and (Re, Im) x_d against the odd ones (Eqs. 7, 9) with
+//                 packed FFMA2.  No pair spectrum leaves registers.
+//   4. reduce   : the C chunk lanes of a slot reduce-scatter their partial
+//                 projections with warp shuffles; lane q keeps pair q.
+//   5. output   : y(tau) on the lag grid from the 2K coefficients -- the grid is
+//                 symmetric, so one pass over tau >= 0 gives y(tau) and y(-tau)
+//                 -- argmax (lowest index wins ties), peak, and the three-point
+//                 quadratic refinement (differences formed exactly in FP64).
 // HBM traffic is the spectra read once plus the per-pair results.
 #include <algorithm>
 #include <cfloat>
@@ -36,35 +41,62 @@
 namespace fcc {
 namespace {
 
-
-// Registers are split per SM sub-partition (16K each, warps assigned round
-// robin), so the register cap and the warp count must fit together:
-// KH = 8 keeps up to 224 registers with at most 8 warps (7 compute + producer);
-// smaller KH cap registers at 168 and allow 8 compute warps + producer.
-__host__ __device__ constexpr int max_compute_warps(int kh) { return kh == 8 ? 7 : 8; }
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kMaxRowSlots = 8;                  // fold records per lane per row: N <= 1024
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
+// Registers are split per SM sub-partition (16K each), so the warp count and
+// the register cap must fit together: KH >= 6 keeps up to 255 registers with 8
+// warps; smaller KH caps registers at 168 with 12 warps.
+__host__ __device__ constexpr int max_compute_warps(int kh) { return kh >= 6 ? 8 : 12; }
+
+// ---- packed FP32 pairs (f32x2 register pairs)
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---- mbarrier / bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 {
     uint32_t ok;
@@ -77,19 +109,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
-
 // Bounded wait on an mbarrier phase; false if it did not complete in time.
 __device__ bool mbar_wait(uint64_t *bar, unsigned parity)
 {
     if (mbar_try_wait(bar, parity)) return true;
-    long long t0 = clock64();
+    const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (clock64() - t0 > kWaitCycles) return false;
         __nanosleep(64);
     }
 }
-
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
 {
     asm volatile(
@@ -98,38 +128,34 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // u = x / |x| with u = 0 for x = 0; scaled slow path for |x|^2 outside the
 // normal FP32 range; flags NaN / Inf.
 __device__ __forceinline__ float2 unit_phase(float2 x, bool &bad)
 {
-    float s = fmaf(x.x, x.x, x.y * x.y);
+    const float s = fmaf(x.x, x.x, x.y * x.y);
     if (s >= FLT_MIN && s <= FLT_MAX) {
-        float r = rsqrtf(s);
+        const float r = rsqrtf(s);
         return make_float2(x.x * r, x.y * r);
     }
-    if (!(fabsf(x.x) <= FLT_MAX) || !(fabsf(x.y) <= FLT_MAX)) {  // NaN or Inf
+    if (!(fabsf(x.x) <= FLT_MAX) || !(fabsf(x.y) <= FLT_MAX)) {
         bad = true;
         return make_float2(0.f, 0.f);
     }
-    float m = fmaxf(fabsf(x.x), fabsf(x.y));
+    const float m = fmaxf(fabsf(x.x), fabsf(x.y));
     if (m == 0.f) return make_float2(0.f, 0.f);
-    float a = x.x / m, b = x.y / m;
-    float r = rsqrtf(fmaf(a, a, b * b));
+    const float a = x.x / m, b = x.y / m;
+    const float r = rsqrtf(fmaf(a, a, b * b));
     return make_float2(a * r, b * r);
 }
 
 struct SmemLayout {
-    size_t bar_off, slot_off, basis_off, stage_off, stage_bytes, total;
+    size_t bar_off, slot_off, basis_off, recon_off, stage_off, stage_bytes, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int S, int n_slots, int Q, int kh, int F,
-                                                  int frame_bytes)
+__host__ __device__ inline SmemLayout smem_layout(int S, int n_slots, int Q, int kh, int C, int BS, int center,
+                                                  int F, int frame_bytes)
 {
     SmemLayout L;
     size_t o = 0;
@@ -140,7 +166,10 @@ __host__ __device__ inline SmemLayout smem_layout(int S, int n_slots, int Q, int
     o += (size_t)n_slots * sizeof(Slot);
     o = (o + 15) & ~(size_t)15;
     L.basis_off = o;
-    o += (size_t)(Q + 1) * 2 * kh * sizeof(float);
+    o += (size_t)(Q + C + 1) * BS * sizeof(float);
+    o = (o + 15) & ~(size_t)15;
+    L.recon_off = o;
+    o += (size_t)(center + 1) * 4 * kh * sizeof(float);
     o = (o + 127) & ~(size_t)127;
     L.stage_off = o;
     L.stage_bytes = (((size_t)F * frame_bytes) + 127) & ~(size_t)127;
@@ -149,255 +178,347 @@ __host__ __device__ inline SmemLayout smem_layout(int S, int n_slots, int Q, int
     return L;
 }
 
-// y at lag index center+m (sign -1) or center-m (sign +1) from the 2K
-// coefficients: S(m) -/+ D(m) (see the recon table layout in pack_tables).
+// Records of rows R = 2, 4, 6 (mod 8) are stored with bit 2 of their index
+// flipped.  Row R's record 0 sits in 16-byte bank group ceil(R/2) mod 8; with the
+// flip, the 8 rows of a frame at one bin pair fall into 8 different bank groups,
+// so a quarter-warp reading one bin pair of several rows is conflict-free.
+__device__ __forceinline__ int rec_swz(int R, int Q) { return (Q >= 8 && !(R & 1) && (R & 7)) ? 4 : 0; }
+
+// Byte offsets, inside a tile, of row R's fold records and of its lone bin N/4.
+__device__ __forceinline__ int rec_off(int R, int B) { return R * B * 8 + ((R & 1) ? 8 : 0); }
+__device__ __forceinline__ int lone_off(int R, int B, int Q) { return R * B * 8 + ((R & 1) ? 0 : 16 * Q); }
+
+// S(m) and D(m) for tau = m / den >= 0 from the packed coefficients:
+// y(center + m) = S - D, y(center - m) = S + D.  Table row m holds, per k,
+// (gSe, gDe, gSo, gDo), matching the packs zE[k] = (Re z_e, Im z_e) and
+// zO[k] = (Re z_o, Im z_o).
 template <int KH>
-__device__ __forceinline__ void eval_SD(const float *__restrict__ recon, int m, const float *z,
-                                        float &S, float &D)
+__device__ __forceinline__ void eval_SD(const float *recon, int m, const f2 *zE, const f2 *zO, float &S, float &D)
 {
-    const float *g = recon + (size_t)m * 4 * KH;
-    float s = 0.f, d = 0.f;
+    const float4 *g = reinterpret_cast<const float4 *>(recon + (size_t)m * 4 * KH);
+    f2 sd = 0ull;
 #pragma unroll
     for (int k = 0; k < KH; ++k) {
-        s = fmaf(__ldg(g + k), z[k], s);
-        s = fmaf(__ldg(g + KH + k), z[2 * KH + k], s);
-        d = fmaf(__ldg(g + 2 * KH + k), z[KH + k], d);
-        d = fmaf(__ldg(g + 3 * KH + k), z[3 * KH + k], d);
+        const float4 v = g[k];
+        sd = fma2(pk(v.x, v.y), zE[k], sd);
+        sd = fma2(pk(v.z, v.w), zO[k], sd);
     }
-    S = s;
-    D = d;
+    upk(sd, S, D);
 }
 
 template <int KH>
-__device__ __forceinline__ float y_at(const float *__restrict__ recon, int center, int i, const float *z)
+__device__ __forceinline__ float y_at(const float *recon, int center, int i, const f2 *zE, const f2 *zO)
 {
-    int m = i >= center ? i - center : center - i;
+    const int m = i >= center ? i - center : center - i;
     float S, D;
-    eval_SD<KH>(recon, m, z, S, D);
+    eval_SD<KH>(recon, m, zE, zO, S, D);
     return i >= center ? S - D : S + D;
 }
 
 template <int KH>
-__global__ void __maxnreg__(KH == 8 ? 224 : 168) fcc_fp32_kernel(const Fp32Params p)
+__global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel(const Fp32Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const SmemLayout lay = smem_layout(p.S, p.n_slots, p.Q, KH, p.F, p.frame_floats * 4);
+    const int frame_bytes = p.frame_floats * 4;
+    const SmemLayout lay = smem_layout(p.S, p.n_slots, p.Q, KH, p.C, p.BS, p.center, p.F, frame_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bar_off);
-    uint64_t *empty = full + p.S;
-    uint64_t *normd = empty + p.S;  // group-wide "stage normalised" barrier
+    uint64_t *normd = full + p.S;   // group: every row of the tile re-laid
+    uint64_t *freed = normd + p.S;  // group: every warp left the tile's rows
     Slot *slots = reinterpret_cast<Slot *>(smem + lay.slot_off);
     float *basis = reinterpret_cast<float *>(smem + lay.basis_off);
+    float *recon = reinterpret_cast<float *>(smem + lay.recon_off);
     unsigned char *stages = smem + lay.stage_off;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_compute_warps = p.G * p.GW;
+    const int group = warp / p.GW, wig = warp - group * p.GW;
     const int n_local = (p.n_tiles > (int)blockIdx.x)
                             ? (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                             : 0;
+    const bool leader = (wig == 0 && lane == 0);
 
-    // ---- prologue: barriers, slot table and bases into shared memory
+    // ---- prologue: barriers, tables into shared memory
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.S; ++s) {
-            mbar_init(&full[s], p.bulk ? 1u : 32u);
-            mbar_init(&empty[s], (unsigned)p.GW);
+            mbar_init(&full[s], p.bulk ? 1u : (unsigned)(p.GW * 32));
             mbar_init(&normd[s], (unsigned)p.GW);
+            mbar_init(&freed[s], (unsigned)p.GW);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
-    {
-        const int nb = (p.Q + 1) * 2 * KH;
-        for (int e = threadIdx.x; e < nb; e += blockDim.x) basis[e] = p.basis[e];
-    }
+    for (int e = threadIdx.x; e < (p.Q + p.C + 1) * p.BS; e += blockDim.x) basis[e] = p.basis[e];
+    for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
     fence_proxy_async();
     __syncthreads();
 
-    if (warp == n_compute_warps) {
-        // ================= producer warp =================
-        const size_t frame_bytes = (size_t)p.frame_floats * 4;
-        int issued = 0;
-        bool ok = true;
-        for (int k = 0; k < n_local && ok; ++k) {
-            const int s = k % p.S;
-            const unsigned par = ((unsigned)(k / p.S) & 1u) ^ 1u;
-            if (!mbar_wait(&empty[s], par)) {
-                ok = false;
-                break;
-            }
-            const long long tile = (long long)blockIdx.x + (long long)k * gridDim.x;
-            const long long f0 = tile * p.F;
-            const int nf = (int)min((long long)p.F, p.T - f0);
-            const char *src = reinterpret_cast<const char *>(p.spectra) + (size_t)f0 * frame_bytes;
-            unsigned char *dst = stages + (size_t)s * lay.stage_bytes;
-            const size_t bytes = (size_t)nf * frame_bytes;
-            if (p.bulk) {
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], (unsigned)bytes);
-                    bulk_g2s(dst, src, (unsigned)bytes, &full[s]);
-                }
-            } else {
-                const size_t n8 = bytes / 8;
-                const unsigned long long *s8 = reinterpret_cast<const unsigned long long *>(src);
-                unsigned long long *d8 = reinterpret_cast<unsigned long long *>(dst);
-                for (size_t e = lane; e < n8; e += 32) d8[e] = __ldg(s8 + e);
-                mbar_arrive(&full[s]);
-            }
-            ++issued;
-        }
-        if (!ok && lane == 0) atomicOr(p.err, kErrTimeout);
-        // never leave a bulk copy in flight when the CTA retires
-        if (p.bulk && lane == 0) {
-            for (int k = max(0, issued - p.S); k < issued; ++k)
-                if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u)) atomicOr(p.err, kErrTimeout);
-        }
-        return;
-    }
+    auto tile_src = [&](int k, int &nf) {
+        const long long tile = (long long)blockIdx.x + (long long)k * gridDim.x;
+        const long long f0 = tile * p.F;
+        nf = (int)min((long long)p.F, p.T - f0);
+        return f0;
+    };
+    // Issue the bulk copy of this CTA's tile k into its stage (group leader only).
+    auto issue = [&](int k) {
+        int nf;
+        const long long f0 = tile_src(k, nf);
+        const int s = k % p.S;
+        const unsigned bytes = (unsigned)nf * (unsigned)frame_bytes;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(stages + (size_t)s * lay.stage_bytes,
+                 reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes, bytes, &full[s]);
+    };
 
-    // ================= consumer groups =================
-    const int group = warp / p.GW;
-    const int lane_g = (warp % p.GW) * 32 + lane;
-    const int gthreads = p.GW * 32;
+    // prime this group's stages
+    const int Sg = p.S / p.G;
+    if (p.bulk && leader)
+        for (int j = 0; j < Sg; ++j)
+            if (group + j * p.G < n_local) issue(group + j * p.G);
+
+    // lane -> (frame in tile, slot, chunk).  A frame takes n_blocks whole warps;
+    // inside a warp the lanes are chunk-major (lane = chunk * SB + slot), so the
+    // 32 / SB lanes of a quarter-warp share one chunk and read one basis row.
+    const int lane_g = wig * 32 + lane;
     const int fl = lane_g / p.lanes_frame;
     const int rem = lane_g - fl * p.lanes_frame;
-    const int slot_id = rem / p.C;
-    const int chunk = rem - slot_id * p.C;
+    const int chunk = (rem & 31) / p.SB;
+    const int slot_id = (rem >> 5) * p.SB + (rem & 31) % p.SB;
     const int QC = p.Q / p.C;
-    const int B = p.B;
-    const int half = 2 * p.Q;  // N/2
+    const int B = p.B, Q = p.Q, M = p.M;
     const unsigned FULLM = 0xffffffffu;
+    int k_done = group - p.G;  // last tile fully consumed by this group
 
     for (int k = group; k < n_local; k += p.G) {
         const int s = k % p.S;
-        if (!mbar_wait(&full[s], (unsigned)(k / p.S) & 1u)) {
+        const unsigned par = (unsigned)(k / p.S) & 1u;
+        int nf;
+        const long long f0 = tile_src(k, nf);
+        unsigned char *st = stages + (size_t)s * lay.stage_bytes;
+        if (!p.bulk) {
+            // plain-load staging (frame size not a multiple of 16 bytes)
+            const size_t n8 = (size_t)nf * frame_bytes / 8;
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(
+                reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(st);
+            for (size_t e = lane_g; e < n8; e += p.GW * 32) dst[e] = __ldg(src + e);
+            mbar_arrive(&full[s]);
+        }
+        if (!mbar_wait(&full[s], par)) {
             if (lane == 0) atomicOr(p.err, kErrTimeout);
             break;
         }
-        const long long tile = (long long)blockIdx.x + (long long)k * gridDim.x;
-        const long long f0 = tile * p.F;
-        const int nf = (int)min((long long)p.F, p.T - f0);
-        float2 *st = reinterpret_cast<float2 *>(stages + (size_t)s * lay.stage_bytes);
 
-        // ---- 2. PHAT normalisation in place
+        // ---- 2. PHAT + folded re-lay, one row per warp at a time
         {
             bool bad = false;
-            const int ne = nf * p.M * B;
-            for (int e = lane_g; e < ne; e += gthreads) st[e] = unit_phase(st[e], bad);
+            const int rows = nf * M;
+            for (int R = wig; R < rows; R += p.GW) {
+                const float2 *raw = reinterpret_cast<const float2 *>(st + (size_t)R * B * 8);
+                float4 rec[kMaxRowSlots];
+                float2 lone = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < kMaxRowSlots; ++j) {
+                    const int fp = lane + 32 * j;
+                    if (fp < Q) {
+                        const float2 a = unit_phase(raw[fp], bad);
+                        const float2 b = unit_phase(raw[2 * Q - fp], bad);
+                        rec[j] = make_float4(a.x, a.y, b.x, b.y);
+                    }
+                }
+                if (lane == 0) lone = unit_phase(raw[Q], bad);
+                __syncwarp();  // the whole row is read before any of it is rewritten
+                float4 *recs = reinterpret_cast<float4 *>(st + rec_off(R, B));
+                const int sw = rec_swz(R, Q);
+#pragma unroll
+                for (int j = 0; j < kMaxRowSlots; ++j) {
+                    const int fp = lane + 32 * j;
+                    if (fp < Q) recs[fp ^ sw] = rec[j];
+                }
+                if (lane == 0) *reinterpret_cast<float2 *>(st + lone_off(R, B, Q)) = lone;
+                __syncwarp();
+            }
             if (__any_sync(FULLM, bad) && lane == 0) atomicOr(p.err, kErrNonFinite);
         }
-        __syncwarp();
         if (p.GW > 1) {
-            // every warp of the group must see the whole tile normalised
             if (lane == 0) mbar_arrive(&normd[s]);
-            if (!mbar_wait(&normd[s], (unsigned)(k / p.S) & 1u)) {
+            if (!mbar_wait(&normd[s], par)) {
                 if (lane == 0) atomicOr(p.err, kErrTimeout);
                 break;
             }
         }
 
-        // ---- 3. fold + projection over this lane's frequency chunk
+        // ---- 3. fold + projection over this lane's chunk of bin pairs
         const bool active = (fl < nf) && (slot_id < p.n_slots);
-        float acc[4][4 * KH];
+        f2 accE[4][KH], accO[4][KH];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int v = 0; v < 4 * KH; ++v) acc[q][v] = 0.f;
-        Slot sl;
+            for (int v = 0; v < KH; ++v) accE[q][v] = accO[q][v] = 0ull;
+        Slot sl{};
         if (active) {
             sl = slots[slot_id];
-            const float2 *U = st + (size_t)fl * p.M * B;
-            const float2 *ui1 = U + sl.mic[0] * B;
-            const float2 *ui2 = U + sl.mic[1] * B;
-            const float2 *uj1 = U + sl.mic[2] * B;
-            const float2 *uj2 = U + sl.mic[3] * B;
-            const int fbase = chunk * QC;
-            const int r0 = p.rot * chunk;
-#pragma unroll 2
-            for (int it = 0; it < QC; ++it) {
-                const int f = fbase + ((it + r0) & (QC - 1));
-                const int fm = half - f;
-                const float2 xa[2] = {ui1[f], ui2[f]};
-                const float2 ya[2] = {uj1[f], uj2[f]};
-                const float2 xb[2] = {ui1[fm], ui2[fm]};
-                const float2 yb[2] = {uj1[fm], uj2[fm]};
-                // basis row of bin f: even bases in [0, KH), odd bases in [KH, 2KH)
-                float row[2 * KH];
-                const float4 *b4 = reinterpret_cast<const float4 *>(basis + (size_t)f * 2 * KH);
+            const int R0 = fl * M;
+            const float4 *bas = reinterpret_cast<const float4 *>(basis);
+            const int BS4 = p.BS / 4;                   // basis row stride in float4
+            const float4 *bchunk = bas + (size_t)chunk * (QC + 1) * BS4;  // one pad row per chunk
+            auto body = [&](const float4 (&X)[2], const float4 (&Y)[2], const float4 *brow) {
+                f2 bE[KH], bO[KH];
+                float w[2 * KH];
 #pragma unroll
                 for (int v = 0; v < KH / 2; ++v) {
-                    const float4 w = b4[v];
-                    row[4 * v] = w.x;
-                    row[4 * v + 1] = w.y;
-                    row[4 * v + 2] = w.z;
-                    row[4 * v + 3] = w.w;
+                    const float4 e = brow[v];
+                    w[4 * v] = e.x;
+                    w[4 * v + 1] = e.y;
+                    w[4 * v + 2] = e.z;
+                    w[4 * v + 3] = e.w;
                 }
-                const float *be = row, *bo = row + KH;
+#pragma unroll
+                for (int v = 0; v < KH; ++v) {
+                    bE[v] = pk(w[v], w[v]);
+                    bO[v] = pk(w[KH + v], w[KH + v]);
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 x1 = xa[q >> 1], y1 = ya[q & 1];
-                    const float2 x2 = xb[q >> 1], y2 = yb[q & 1];
-                    // a = x1 y1^*, b = x2 y2^*  (cross spectra at f and N/2 - f)
-                    const float ar = fmaf(x1.x, y1.x, x1.y * y1.y);
-                    const float ai = fmaf(x1.y, y1.x, -(x1.x * y1.y));
-                    const float br = fmaf(x2.x, y2.x, x2.y * y2.y);
-                    const float bi = fmaf(x2.y, y2.x, -(x2.x * y2.y));
-                    const float sr = ar + br, si = ai + bi;  // x_s (Eq. 8)
-                    const float dr = ar - br, di = ai - bi;  // x_d (Eq. 8)
+                    const float4 x = X[q >> 1], y = Y[q & 1];
+                    // cross spectra at f and N/2 - f: a = x(f) y(f)^*, b = x(N/2-f) y(N/2-f)^*
+                    const f2 a = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
+                    const f2 b = pk(fmaf(x.z, y.z, x.w * y.w), fmaf(x.w, y.z, -(x.z * y.w)));
+                    const f2 xs = add2(a, b), xd = sub2(a, b);  // Eq. 8
 #pragma unroll
                     for (int v = 0; v < KH; ++v) {
-                        acc[q][v] = fmaf(be[v], sr, acc[q][v]);
-                        acc[q][KH + v] = fmaf(be[v], si, acc[q][KH + v]);
-                        acc[q][2 * KH + v] = fmaf(bo[v], dr, acc[q][2 * KH + v]);
-                        acc[q][3 * KH + v] = fmaf(bo[v], di, acc[q][3 * KH + v]);
+                        accE[q][v] = fma2(bE[v], xs, accE[q][v]);
+                        accO[q][v] = fma2(bO[v], xd, accO[q][v]);
                     }
+                }
+            };
+            const int cb = chunk * QC;
+            const int st_off = (int)(st - smem);
+            int sw[4], rb[4];  // byte offsets from the shared-memory base
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sw[r] = rec_swz(R0 + sl.mic[r], Q);
+                rb[r] = st_off + rec_off(R0 + sl.mic[r], B) + 16 * cb;
+            }
+            if ((QC & 7) == 0) {
+                // 8 records at a time: record cb+t8+j of a swizzled row is at
+                // cb+t8+(j^4), i.e. +4 records for j < 4 and -4 for j >= 4
+                int lo[4], hi[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    lo[r] = rb[r] + 16 * sw[r];
+                    hi[r] = rb[r] - 16 * sw[r];
+                }
+#pragma unroll 1
+                for (int t8 = 0; t8 < QC; t8 += 8) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int o = 16 * (t8 + j);
+                        float4 X[2], Y[2];
+                        X[0] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[0] : hi[0]) + o);
+                        X[1] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[1] : hi[1]) + o);
+                        Y[0] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[2] : hi[2]) + o);
+                        Y[1] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[3] : hi[3]) + o);
+                        body(X, Y, bchunk + (size_t)(t8 + j) * BS4);
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int t = 0; t < QC; ++t) {
+                    float4 X[2], Y[2];
+                    X[0] = *reinterpret_cast<const float4 *>(smem + rb[0] + 16 * (((cb + t) ^ sw[0]) - cb));
+                    X[1] = *reinterpret_cast<const float4 *>(smem + rb[1] + 16 * (((cb + t) ^ sw[1]) - cb));
+                    Y[0] = *reinterpret_cast<const float4 *>(smem + rb[2] + 16 * (((cb + t) ^ sw[2]) - cb));
+                    Y[1] = *reinterpret_cast<const float4 *>(smem + rb[3] + 16 * (((cb + t) ^ sw[3]) - cb));
+                    body(X, Y, bchunk + (size_t)t * BS4);
                 }
             }
             if (chunk == 0) {
-                // f = N/4: x_s = R_hat(N/4); x_d's entry meets only zeros of the odd bases
-                const int f = p.Q;
-                const float2 xa[2] = {ui1[f], ui2[f]};
-                const float2 ya[2] = {uj1[f], uj2[f]};
+                // bin N/4: x_s = R_hat(N/4); the odd bases vanish there (Eq. 8)
+                float2 X[2], Y[2];
+                X[0] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[0], B, Q));
+                X[1] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[1], B, Q));
+                Y[0] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[2], B, Q));
+                Y[1] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[3], B, Q));
+                f2 bE[KH];
+                const float4 *brow = bas + (size_t)p.C * (QC + 1) * BS4;
+#pragma unroll
+                for (int v = 0; v < KH / 4 + (KH % 4 ? 1 : 0); ++v) {
+                    const float4 e = brow[v];
+                    if (4 * v < KH) bE[4 * v] = pk(e.x, e.x);
+                    if (4 * v + 1 < KH) bE[4 * v + 1] = pk(e.y, e.y);
+                    if (4 * v + 2 < KH) bE[4 * v + 2] = pk(e.z, e.z);
+                    if (4 * v + 3 < KH) bE[4 * v + 3] = pk(e.w, e.w);
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 x1 = xa[q >> 1], y1 = ya[q & 1];
-                    const float sr = fmaf(x1.x, y1.x, x1.y * y1.y);
-                    const float si = fmaf(x1.y, y1.x, -(x1.x * y1.y));
+                    const float2 x = X[q >> 1], y = Y[q & 1];
+                    const f2 xs = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
 #pragma unroll
-                    for (int v = 0; v < KH; ++v) {
-                        const float b = basis[(size_t)f * 2 * KH + v];
-                        acc[q][v] = fmaf(b, sr, acc[q][v]);
-                        acc[q][KH + v] = fmaf(b, si, acc[q][KH + v]);
-                    }
+                    for (int v = 0; v < KH; ++v) accE[q][v] = fma2(bE[v], xs, accE[q][v]);
                 }
             }
         }
-        // release the stage: order our generic-proxy writes before the next bulk copy
-        fence_proxy_async();
+        // ---- release the stage and refill it with this group's tile k + S
+        fence_proxy_async();  // our generic writes precede the next bulk write
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        if (p.bulk) {
+            if (p.GW > 1) {
+                if (lane == 0) mbar_arrive(&freed[s]);
+                if (leader && k + p.S < n_local) {
+                    if (!mbar_wait(&freed[s], par)) {
+                        atomicOr(p.err, kErrTimeout);
+                    } else {
+                        issue(k + p.S);
+                    }
+                }
+            } else if (lane == 0 && k + p.S < n_local) {
+                issue(k + p.S);
+            }
+        } else if (p.GW > 1) {
+            // plain staging: the group's next copy must not start before every
+            // warp has left this stage
+            if (lane == 0) mbar_arrive(&freed[s]);
+            if (!mbar_wait(&freed[s], par)) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+        }
+        k_done = k;
 
         // ---- 4. reduce-scatter of the chunk partials: lane (chunk & 3) keeps pair (chunk & 3)
-        float z[4 * KH];
+        f2 zE[KH], zO[KH];
         {
             const bool hi = (chunk & 2) != 0;
-            float r1[2][4 * KH];
+            f2 rE[2][KH], rO[2][KH];
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
-                for (int v = 0; v < 4 * KH; ++v) {
-                    const float mine = hi ? acc[pp + 2][v] : acc[pp][v];
-                    const float other = hi ? acc[pp][v] : acc[pp + 2][v];
-                    r1[pp][v] = mine + __shfl_xor_sync(FULLM, other, 2);
+                for (int v = 0; v < KH; ++v) {
+                    float m0, m1, o0, o1;
+                    upk(hi ? accE[pp + 2][v] : accE[pp][v], m0, m1);
+                    upk(hi ? accE[pp][v] : accE[pp + 2][v], o0, o1);
+                    rE[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
+                    upk(hi ? accO[pp + 2][v] : accO[pp][v], m0, m1);
+                    upk(hi ? accO[pp][v] : accO[pp + 2][v], o0, o1);
+                    rO[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
                 }
             const bool b0 = (chunk & 1) != 0;
 #pragma unroll
-            for (int v = 0; v < 4 * KH; ++v) {
-                const float mine = b0 ? r1[1][v] : r1[0][v];
-                const float other = b0 ? r1[0][v] : r1[1][v];
-                z[v] = mine + __shfl_xor_sync(FULLM, other, 1);
-            }
-            for (int o = 4; o < p.C; o <<= 1) {
-#pragma unroll
-                for (int v = 0; v < 4 * KH; ++v) z[v] += __shfl_xor_sync(FULLM, z[v], o);
+            for (int v = 0; v < KH; ++v) {
+                float m0, m1, o0, o1;
+                upk(b0 ? rE[1][v] : rE[0][v], m0, m1);
+                upk(b0 ? rE[0][v] : rE[1][v], o0, o1);
+                float e0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), e1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
+                upk(b0 ? rO[1][v] : rO[0][v], m0, m1);
+                upk(b0 ? rO[0][v] : rO[1][v], o0, o1);
+                float d0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), d1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
+                for (int o = 4 * p.SB; o < 32; o <<= 1) {
+                    e0 += __shfl_xor_sync(FULLM, e0, o);
+                    e1 += __shfl_xor_sync(FULLM, e1, o);
+                    d0 += __shfl_xor_sync(FULLM, d0, o);
+                    d1 += __shfl_xor_sync(FULLM, d1, o);
+                }
+                zE[v] = pk(e0, e1);
+                zO[v] = pk(d0, d1);
             }
         }
 
@@ -405,16 +526,15 @@ __global__ void __maxnreg__(KH == 8 ? 224 : 168) fcc_fp32_kernel(const Fp32Param
         const int q = chunk & 3;
         const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
         if (active && chunk < 4 && pq >= 0) {
-            const long long t = f0 + fl;
-            const size_t o = (size_t)t * p.P + pq;
+            const size_t o = (size_t)(f0 + fl) * p.P + pq;
             float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
             float S, D;
-            eval_SD<KH>(p.recon, 0, z, S, D);
+            eval_SD<KH>(recon, 0, zE, zO, S, D);
             float best = S - D;
             int bi = p.center;
             if (corr) corr[p.center] = best;
             for (int m = 1; m <= p.center; ++m) {
-                eval_SD<KH>(p.recon, m, z, S, D);
+                eval_SD<KH>(recon, m, zE, zO, S, D);
                 const float ym = S + D, yp = S - D;  // y(center - m), y(center + m)
                 if (ym >= best) {  // lower index than everything seen so far
                     best = ym;
@@ -432,35 +552,42 @@ __global__ void __maxnreg__(KH == 8 ? 224 : 168) fcc_fp32_kernel(const Fp32Param
             p.out_idx[o] = bi;
             p.out_peak[o] = best;
             if (p.out_tau) {
-                double tau = (double)(bi - p.center) * (double)p.delta;
+                float off = 0.f;
                 if (bi > 0 && bi < p.I - 1) {
-                    const double y_m = y_at<KH>(p.recon, p.center, bi - 1, z);
-                    const double y_p = y_at<KH>(p.recon, p.center, bi + 1, z);
-                    const double den = y_m - 2.0 * (double)best + y_p;
-                    if (den < 0.0) {
-                        double d = 0.5 * (y_m - y_p) / den;
-                        d = fmin(0.5, fmax(-0.5, d));
-                        tau += (double)p.delta * d;
-                    }
+                    // three-point parabola; the differences, where the
+                    // cancellation happens, are exact in FP64
+                    const double y_m = y_at<KH>(recon, p.center, bi - 1, zE, zO);
+                    const double y_p = y_at<KH>(recon, p.center, bi + 1, zE, zO);
+                    const double num = y_m - y_p;
+                    const double den = (y_m - 2.0 * (double)best) + y_p;
+                    if (den < 0.0) off = fminf(0.5f, fmaxf(-0.5f, 0.5f * (float)num / (float)den));
                 }
-                p.out_tau[o] = (float)tau;
+                p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
             }
             if (p.out_coef) {
                 const int K = p.KE + p.KO;
                 float *cf = p.out_coef + o * 2 * K;
 #pragma unroll
                 for (int v = 0; v < KH; ++v) {
+                    float a, b;
                     if (v < p.KE) {
-                        cf[v] = z[v];
-                        cf[p.KE + v] = z[KH + v];
+                        upk(zE[v], a, b);
+                        cf[v] = a;
+                        cf[p.KE + v] = b;
                     }
                     if (v < p.KO) {
-                        cf[2 * p.KE + v] = z[2 * KH + v];
-                        cf[2 * p.KE + p.KO + v] = z[3 * KH + v];
+                        upk(zO[v], a, b);
+                        cf[2 * p.KE + v] = a;
+                        cf[2 * p.KE + p.KO + v] = b;
                     }
                 }
             }
         }
+    }
+    // never retire with one of this group's bulk copies still in flight
+    if (p.bulk && leader) {
+        for (int k = k_done + p.G; k < n_local && k <= k_done + p.S; k += p.G)
+            if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u)) atomicOr(p.err, kErrTimeout);
     }
 }
 
@@ -468,15 +595,13 @@ template <int KH>
 fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
 {
     static bool attr_set[64] = {};
-    int dev = plan->device;
+    const int dev = plan->device;
     if (!attr_set[dev & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(fcc_fp32_kernel<KH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        cudaError_t e = cudaFuncSetAttribute(fcc_fp32_kernel<KH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fcc_fp32_kernel)");
         attr_set[dev & 63] = true;
     }
-    const int threads = (prm.G * prm.GW + 1) * 32;
-    fcc_fp32_kernel<KH><<<grid, threads, plan->geo.smem_bytes, st>>>(prm);
+    fcc_fp32_kernel<KH><<<grid, prm.G * prm.GW * 32, plan->geo.smem_bytes, st>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fcc_fp32_kernel launch");
     return FCC_OK;
@@ -485,46 +610,45 @@ fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t
 }  // namespace
 
 // Choose chunks per slot (C), warps per group (GW), groups (G), frames per
-// stage (F) and the ring depth (S) for this plan's M, N and K.  Tile k lives in
-// stage k % S and is processed by group k % G; S is a multiple of G so that
-// every stage is only ever filled for, and released by, one group -- each
-// group then sees a plain single-consumer ring and the mbarrier phase parity
-// it waits on can never be two phases stale.  The environment variables
-// FCC_FP32_GROUPS and FCC_FP32_STAGES_PER_GROUP pin G and S/G (tuning only).
+// stage (F) and the ring depth (S = G * stages per group) for this plan.  Each
+// stage is only ever filled for, and released by, one group, so every group
+// sees a plain single-consumer ring and a phase parity can never be stale.
+// FCC_FP32_GROUPS / FCC_FP32_STAGES_PER_GROUP pin G and S/G (tuning only).
 fcc_status_t choose_fp32_geometry(fcc_plan *plan)
 {
     const fcc_plan_info_t &in = plan->info;
     const int kh = plan->kh;
     const int n_slots = plan->n_slots;
     const int frame_bytes = in.M * in.B * 8;
+    if (in.Q > 32 * kMaxRowSlots) return FCC_OK;  // N > 1024: the FP32 kernel is not used
     int smem_max = 0;
     FCC_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
     smem_max = std::min(smem_max, 232448);
     const char *eg = getenv("FCC_FP32_GROUPS");
     const char *es = getenv("FCC_FP32_STAGES_PER_GROUP");
     const int want_g = eg ? atoi(eg) : 0, want_sg = es ? atoi(es) : 0;
+    // basis row: KH even then KH odd weights, padded to an odd number of 16-byte units
+    const int BS = ((2 * kh / 4) % 2 == 0) ? 2 * kh + 4 : 2 * kh;
+    const int maxw = max_compute_warps(kh);
     Fp32Geometry best{};
     double best_score = -1.0;
     for (int C = 4; C <= 16 && C <= in.Q; C <<= 1) {
-        const int lanes = n_slots * C;
-        for (int GW = 1; GW <= max_compute_warps(kh); GW <<= 1) {
-            if (lanes > GW * 32) continue;
-            const int F = (GW * 32) / lanes;
-            for (int G = max_compute_warps(kh) / GW; G >= 1; --G) {
+        const int SB = 32 / C;
+        const int nb = (n_slots + SB - 1) / SB;
+        const double util = (double)n_slots / (nb * SB);
+        for (int F = 1; nb * F <= maxw; ++F) {
+            const int GW = nb * F;
+            for (int G = maxw / GW; G >= 1; --G) {
                 if (want_g && G != want_g) continue;
-                for (int Sg = 3; Sg >= 1; --Sg) {
+                for (int Sg = 2; Sg >= 1; --Sg) {
                     if (want_sg && Sg != want_sg) continue;
                     const int S = G * Sg;
-                    const SmemLayout L = smem_layout(S, n_slots, in.Q, kh, F, frame_bytes);
+                    const SmemLayout L = smem_layout(S, n_slots, in.Q, kh, C, BS, in.center, F, frame_bytes);
                     if (L.total > (size_t)smem_max) continue;
-                    // lane utilisation x warps in flight; a group with a second
-                    // stage can prefetch while it computes; fewer chunks reduce
-                    // the shuffle reduction
-                    const double util = (double)(F * lanes) / (GW * 32);
-                    const double score = util * (G * GW) * (Sg >= 2 ? 1.0 : 0.8) * (1.0 - 0.02 * (C / 4 - 1));
+                    const double score = util * (G * GW) * (Sg >= 2 ? 1.05 : 1.0) * (1.0 - 0.02 * (C / 4 - 1));
                     if (score > best_score) {
                         best_score = score;
-                        best = Fp32Geometry{C, lanes, GW, G, F, S, 5, L.total};
+                        best = Fp32Geometry{C, SB, nb * 32, GW, G, F, S, BS, L.total};
                     }
                     break;  // the deepest ring that fits for this G
                 }
@@ -536,11 +660,12 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan)
     return FCC_OK;
 }
 
-fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,
-                         float *peak, float *tau, float *coef, float *corr, cudaStream_t st)
+fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                         float *tau, float *coef, float *corr, cudaStream_t st)
 {
     const fcc_plan_info_t &in = plan->info;
     const Fp32Geometry &g = plan->geo;
+    if (g.G == 0) return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
     Fp32Params prm{};
     prm.spectra = spectra;
     prm.T = T;
@@ -551,12 +676,13 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     prm.P = in.P;
     prm.n_slots = plan->n_slots;
     prm.C = g.C;
+    prm.SB = g.SB;
+    prm.BS = g.BS;
     prm.lanes_frame = g.lanes_frame;
     prm.GW = g.GW;
     prm.G = g.G;
     prm.F = g.F;
     prm.S = g.S;
-    prm.rot = g.rot;
     const long long n_tiles = (T + g.F - 1) / g.F;
     if (n_tiles > 0x7fffffffLL) return fail(FCC_ERR_UNSUPPORTED, "too many frames for one call");
     prm.n_tiles = (int)n_tiles;
@@ -567,7 +693,6 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     prm.I = in.I;
     prm.KE = in.K_even;
     prm.KO = in.K_odd;
-    prm.tau0 = (float)(-in.L);
     prm.delta = (float)in.delta;
     prm.basis = plan->d_basis;
     prm.recon = plan->d_recon;

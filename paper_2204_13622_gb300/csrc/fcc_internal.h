@@ -57,12 +57,13 @@ struct Slot {
 // Launch geometry of the FP32 kernel, chosen on the host per plan.
 struct Fp32Geometry {
     int C;            // frequency chunks per slot (lanes that share one slot)
-    int lanes_frame;  // n_slots * C
+    int SB;           // slots per warp (32 / C); a warp's lanes are chunk-major
+    int lanes_frame;  // lanes per frame: whole warps, ceil(n_slots / SB) * 32
     int GW;           // warps per group
     int G;            // groups per CTA
     int F;            // frames per stage (tile)
-    int S;            // stages in the shared-memory ring
-    int rot;          // chunk-dependent rotation of the frequency loop (bank spread)
+    int S;            // stages in the shared-memory ring (a multiple of G)
+    int BS;           // basis row stride in floats (an odd number of 16-byte units)
     size_t smem_bytes;
 };
 
@@ -71,14 +72,14 @@ struct Fp32Params {
     const float2 *spectra;  // [T][M][B]
     long long T;
     int M, B, Q, N, P;
-    int n_slots, C, lanes_frame, GW, G, F, S, rot;
+    int n_slots, C, SB, lanes_frame, GW, G, F, S, BS;
     int n_tiles;
     int frame_floats;       // M * B * 2
     int bulk;               // 1: cp.async.bulk staging, 0: plain-load staging
     int center, I, KE, KO;  // KE/KO: actual basis counts (<= KH)
-    float tau0, delta;
-    const float *basis;     // [Q+1][2*KH]: even bases then odd bases per bin
-    const float *recon;     // [center+1][4][KH]: gSe, gSo, gDe, gDo
+    float delta;
+    const float *basis;     // [Q+C+1][BS]: per chunk QC rows + one zero row, then bin N/4
+    const float *recon;     // [center+1][KH][4]: (gSe, gDe, gSo, gDo) per k
     const Slot *slots;      // [n_slots]
     int *out_idx;
     float *out_peak;
