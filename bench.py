@@ -232,7 +232,8 @@ def run_fcc(args, rank, world, local):
         if rank == 0:
             res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                    "warmup": args.warmup, "ms_per_step": ms_max, "config": {"workload": w.name, "frames": T},
-                   "note": "FCC kernel only (profiling run)", "roofline_achieved_gbs": achieved}
+                   "note": "FCC kernel only (profiling run)", "roofline_achieved_gbs": achieved,
+                   "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
         plan.close()
         return res
 
@@ -274,10 +275,17 @@ def run_fcc(args, rank, world, local):
     if rank == 0:
         cpu, _, _ = oracle_rate(w, float(os.environ.get("FCC_CPU_BASELINE_SECONDS", "12")),
                                 lambda n: Xh[:n].numpy())
+        # DRAM bytes per launch from the committed ncu capture, valid only while
+        # the kernel source is the one that was captured
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tfile):
-            traffic = json.load(open(tfile)).get("fcc_fp32_kernel_circle8_bytes_per_launch")
+            import hashlib
+            rec = json.load(open(tfile))
+            src = os.path.join(ROOT, "paper_2204_13622_gb300", "csrc", "fcc_fp32.cu")
+            if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec.get(
+                    "fcc_fp32_kernel_source_sha256_16"):
+                traffic = rec.get("fcc_fp32_kernel_circle8_bytes_per_launch")
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",

@@ -1,6 +1,8 @@
 // fcc_api.cu -- the extern "C" entry points declared in include/fcc.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -260,6 +262,10 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
         free_plan(p);
         return cuda_fail(e, "plan tables");
     }
+    if (getenv("FCC_DEBUG"))
+        fprintf(stderr, "[fcc] plan M=%d N=%d I=%d K=%d (%d+%d) kh=%d slots=%d fp32: C=%d SB=%d GW=%d G=%d F=%d S=%d smem=%zu\n",
+                in.M, in.N, in.I, in.K, in.K_even, in.K_odd, p->kh, p->n_slots, p->geo.C, p->geo.SB, p->geo.GW,
+                p->geo.G, p->geo.F, p->geo.S, p->geo.smem_bytes);
     *out = p;
     return FCC_OK;
 }

@@ -42,7 +42,7 @@ namespace fcc {
 namespace {
 
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
-constexpr int kMaxRowSlots = 8;                  // fold records per lane per row: N <= 1024
+constexpr int kMaxRowSlots = 8;                  // fold records per lane per row (RS): N <= 1024
 
 // Registers are split per SM sub-partition (16K each), so the warp count and
 // the register cap must fit together: KH >= 6 keeps up to 255 registers with 8
@@ -130,9 +130,18 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// u = x / |x| with u = 0 for x = 0; scaled slow path for |x|^2 outside the
-// normal FP32 range; flags NaN / Inf.
-__device__ __forceinline__ float2 unit_phase(float2 x, bool &bad)
+// u = x / |x|.  Fast path for |x|^2 in the normal FP32 range; `ok` reports
+// whether it applied (callers take unit_phase_slow, warp-uniformly, otherwise).
+__device__ __forceinline__ float2 unit_phase_fast(float2 x, bool &ok)
+{
+    const float s = fmaf(x.x, x.x, x.y * x.y);
+    ok = (s >= FLT_MIN) && (s <= FLT_MAX);
+    const float r = rsqrtf(s);
+    return make_float2(x.x * r, x.y * r);
+}
+// u = x / |x| with u = 0 for x = 0; rescaled for |x|^2 outside the normal FP32
+// range; flags NaN / Inf (u = 0).
+__device__ __noinline__ float2 unit_phase_slow(float2 x, bool &bad)
 {
     const float s = fmaf(x.x, x.x, x.y * x.y);
     if (s >= FLT_MIN && s <= FLT_MAX) {
@@ -215,7 +224,8 @@ __device__ __forceinline__ float y_at(const float *recon, int center, int i, con
     return i >= center ? S - D : S + D;
 }
 
-template <int KH>
+// RS = fold records per lane per row = max(1, N / 128) (N/4 records over 32 lanes).
+template <int KH, int RS>
 __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel(const Fp32Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -313,25 +323,41 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
             const int rows = nf * M;
             for (int R = wig; R < rows; R += p.GW) {
                 const float2 *raw = reinterpret_cast<const float2 *>(st + (size_t)R * B * 8);
-                float4 rec[kMaxRowSlots];
-                float2 lone = make_float2(0.f, 0.f);
+                float2 a[RS], b[RS], lone = make_float2(0.f, 0.f);
+                bool ok = true;
 #pragma unroll
-                for (int j = 0; j < kMaxRowSlots; ++j) {
+                for (int j = 0; j < RS; ++j) {
                     const int fp = lane + 32 * j;
-                    if (fp < Q) {
-                        const float2 a = unit_phase(raw[fp], bad);
-                        const float2 b = unit_phase(raw[2 * Q - fp], bad);
-                        rec[j] = make_float4(a.x, a.y, b.x, b.y);
+                    if (RS > 1 || fp < Q) {
+                        bool o1, o2;
+                        a[j] = unit_phase_fast(raw[fp], o1);
+                        b[j] = unit_phase_fast(raw[2 * Q - fp], o2);
+                        ok = ok && o1 && o2;
                     }
                 }
-                if (lane == 0) lone = unit_phase(raw[Q], bad);
+                if (lane == 0) {
+                    bool o;
+                    lone = unit_phase_fast(raw[Q], o);
+                    ok = ok && o;
+                }
+                if (!__all_sync(FULLM, ok)) {  // rare: zero, tiny, huge or non-finite bins
+#pragma unroll
+                    for (int j = 0; j < RS; ++j) {
+                        const int fp = lane + 32 * j;
+                        if (RS > 1 || fp < Q) {
+                            a[j] = unit_phase_slow(raw[fp], bad);
+                            b[j] = unit_phase_slow(raw[2 * Q - fp], bad);
+                        }
+                    }
+                    if (lane == 0) lone = unit_phase_slow(raw[Q], bad);
+                }
                 __syncwarp();  // the whole row is read before any of it is rewritten
                 float4 *recs = reinterpret_cast<float4 *>(st + rec_off(R, B));
                 const int sw = rec_swz(R, Q);
 #pragma unroll
-                for (int j = 0; j < kMaxRowSlots; ++j) {
+                for (int j = 0; j < RS; ++j) {
                     const int fp = lane + 32 * j;
-                    if (fp < Q) recs[fp ^ sw] = rec[j];
+                    if (RS > 1 || fp < Q) recs[fp ^ sw] = make_float4(a[j].x, a[j].y, b[j].x, b[j].y);
                 }
                 if (lane == 0) *reinterpret_cast<float2 *>(st + lone_off(R, B, Q)) = lone;
                 __syncwarp();
@@ -358,7 +384,7 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
             sl = slots[slot_id];
             const int R0 = fl * M;
             const float4 *bas = reinterpret_cast<const float4 *>(basis);
-            const int BS4 = p.BS / 4;                   // basis row stride in float4
+            constexpr int BS4 = ((KH / 2) % 2 == 0) ? KH / 2 + 1 : KH / 2;  // basis row stride in float4 (odd)
             const float4 *bchunk = bas + (size_t)chunk * (QC + 1) * BS4;  // one pad row per chunk
             auto body = [&](const float4 (&X)[2], const float4 (&Y)[2], const float4 *brow) {
                 f2 bE[KH], bO[KH];
@@ -591,20 +617,34 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
     }
 }
 
-template <int KH>
-fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
+template <int KH, int RS>
+fcc_status_t launch_inst(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
 {
     static bool attr_set[64] = {};
     const int dev = plan->device;
     if (!attr_set[dev & 63]) {
-        cudaError_t e = cudaFuncSetAttribute(fcc_fp32_kernel<KH>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        cudaError_t e = cudaFuncSetAttribute(fcc_fp32_kernel<KH, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             232448);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fcc_fp32_kernel)");
         attr_set[dev & 63] = true;
     }
-    fcc_fp32_kernel<KH><<<grid, prm.G * prm.GW * 32, plan->geo.smem_bytes, st>>>(prm);
+    fcc_fp32_kernel<KH, RS><<<grid, prm.G * prm.GW * 32, plan->geo.smem_bytes, st>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fcc_fp32_kernel launch");
     return FCC_OK;
+}
+
+template <int KH>
+fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
+{
+    const int rs = prm.Q <= 32 ? 1 : prm.Q / 32;
+    switch (rs) {
+    case 1: return launch_inst<KH, 1>(plan, prm, st, grid);
+    case 2: return launch_inst<KH, 2>(plan, prm, st, grid);
+    case 4: return launch_inst<KH, 4>(plan, prm, st, grid);
+    case 8: return launch_inst<KH, 8>(plan, prm, st, grid);
+    default: return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
+    }
 }
 
 }  // namespace
@@ -645,7 +685,11 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan)
                     const int S = G * Sg;
                     const SmemLayout L = smem_layout(S, n_slots, in.Q, kh, C, BS, in.center, F, frame_bytes);
                     if (L.total > (size_t)smem_max) continue;
-                    const double score = util * (G * GW) * (Sg >= 2 ? 1.05 : 1.0) * (1.0 - 0.02 * (C / 4 - 1));
+                    // resident warps first (measured on the 8-mic circle: 12 warps of
+                    // one frame each beat 6 pairs of warps with double-buffered
+                    // stages by 1.4x); fewer chunks mean a shorter shuffle
+                    // reduction; a second stage per group only breaks ties
+                    const double score = util * (G * GW) * (1.0 - 0.1 * (C / 4 - 1)) + (Sg >= 2 ? 0.01 : 0.0);
                     if (score > best_score) {
                         best_score = score;
                         best = Fp32Geometry{C, SB, nb * 32, GW, G, F, S, BS, L.total};
