@@ -186,17 +186,40 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def accuracy_vs_oracle(w, plan, X, out, n=128):
+    """Argmax agreement and peak error against the FP64 oracle on n sampled frames."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    T = X.shape[0]
+    frames = torch.from_numpy(np.linspace(0, T - 1, n).astype(np.int64)).to(X.device)
+    Xs = X[frames].cpu().numpy()
+    ref = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+    idx, peak, _, y = O.tdoa(Xs, ref.WK, ref.taus, ref.delta, want_y=True)
+    gi = out["lag_idx"][frames].cpu().numpy()
+    gp = out["peak"][frames].cpu().numpy()
+    scale = np.abs(y).max(-1)
+    srt = np.sort(y, -1)
+    clear = (srt[..., -1] - srt[..., -2]) / scale > 4e-6
+    return {"frames_sampled": n, "pair_frames": int(gi.size),
+            "argmax_agreement": float((gi == idx).mean()),
+            "argmax_agreement_clear": float((gi == idx)[clear].mean()),
+            "peak_rel_err_median": float(np.median(np.abs(gp - peak) / scale)),
+            "peak_rel_err_max": float(np.max(np.abs(gp - peak) / scale))}
+
+
 def run_fcc(args, rank, world, local):
     import torch
 
     from paper_2204_13622_gb300 import binding, flops, workloads
-    w = workloads.CIRCLE8
+    w = {"circle8": workloads.CIRCLE8, "grid16": workloads.GRID16, "square4": workloads.SQUARE4}[args.workload]
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
     X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
-    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local)
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, prec=args.prec)
     out = plan.tdoa(X, tau_hat=True)  # allocates the outputs once
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 3)):
@@ -222,6 +245,7 @@ def run_fcc(args, rank, world, local):
 
     # ---- roofline of the dominant (only) kernel: algorithmic bytes per launch
     bytes_per_launch = T * (w.M * w.B * 8) + T * P * 12  # spectra read + idx/peak/tau_hat written
+    acc = accuracy_vs_oracle(w, plan, X, out) if rank == 0 else None
     achieved = bytes_per_launch / (ms / 1000.0) / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -233,6 +257,9 @@ def run_fcc(args, rank, world, local):
             res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                    "warmup": args.warmup, "ms_per_step": ms_max, "config": {"workload": w.name, "frames": T},
                    "note": "FCC kernel only (profiling run)", "roofline_achieved_gbs": achieved,
+                   "dtype": args.prec, "roofline_frac": achieved / float(json.load(open(os.path.join(
+                       ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) if os.path.exists(os.path.join(
+                           ROOT, "MEASURED_PEAKS.json")) else None, "accuracy_vs_oracle": acc,
                    "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
         plan.close()
         return res
@@ -279,7 +306,7 @@ def run_fcc(args, rank, world, local):
         # the kernel source is the one that was captured
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tfile):
+        if os.path.exists(tfile) and args.workload == "circle8" and args.prec == "fp32":
             import hashlib
             rec = json.load(open(tfile))
             src = os.path.join(ROOT, "paper_2204_13622_gb300", "csrc", "fcc_fp32.cu")
@@ -289,7 +316,8 @@ def run_fcc(args, rank, world, local):
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16"}[args.prec],
+            "data": "synthetic", "accuracy_vs_oracle": acc,
             "config": {"workload": w.name if T == w.T else f"{w.name} truncated to {T} frames",
                        "frames": T, "mics": w.M, "pairs": P, "N": w.N,
                        "lag_grid": f"[-{w.L}, {w.L}] step 1/{w.lag_den} (I={plan.I})",
@@ -298,7 +326,8 @@ def run_fcc(args, rank, world, local):
                        "l2": "inputs (17.25 GB) larger than L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "fcc_fp32_kernel", "bytes_per_launch": bytes_per_launch,
+                         "kernel": "fcc_fp32_kernel" if args.prec == "fp32" else "fcc_tc_kernel",
+                         "bytes_per_launch": bytes_per_launch,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
             "gcc_phat": {"value": world * T * P / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms,
                          "r": w.lag_den, "argmax_agreement_with_fcc": agree},
@@ -322,6 +351,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="fcc", choices=["fcc", "reference"])
     ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
     ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
+    ap.add_argument("--workload", default="circle8", choices=["circle8", "grid16", "square4"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -116,6 +116,8 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_recon);
     cudaFree(p->d_slots);
     cudaFree(p->d_err);
+    cudaFree(p->d_tc_bases);
+    cudaFree(p->d_tc_peq);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->d_stage[b]);
         cudaFree(p->d_stage_idx[b]);
@@ -143,7 +145,6 @@ fcc_status_t fcc::plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t 
         return fail(FCC_ERR_INVALID_ARG, "N must be a power of two in [16, 4096]");
     if (d->lag_den < 1 || d->lag_den > 64) return fail(FCC_ERR_INVALID_ARG, "lag_den out of [1, 64]");
     if (d->prec < FCC_PREC_FP32 || d->prec > FCC_PREC_FP16) return fail(FCC_ERR_INVALID_ARG, "prec");
-    if (d->prec != FCC_PREC_FP32) return fail(FCC_ERR_UNSUPPORTED, "only FCC_PREC_FP32 in this build");
     if (d->K < 0) return fail(FCC_ERR_INVALID_ARG, "K < 0");
     const double c = d->c > 0 ? d->c : 343.0;
     int L;
@@ -262,6 +263,13 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
         free_plan(p);
         return cuda_fail(e, "plan tables");
     }
+    if (in.prec != FCC_PREC_FP32) {
+        st = prepare_tc(p);
+        if (st != FCC_OK) {
+            free_plan(p);
+            return st;
+        }
+    }
     if (getenv("FCC_DEBUG"))
         fprintf(stderr, "[fcc] plan M=%d N=%d I=%d K=%d (%d+%d) kh=%d slots=%d fp32: C=%d SB=%d GW=%d G=%d F=%d S=%d smem=%zu\n",
                 in.M, in.N, in.I, in.K, in.K_even, in.K_odd, p->kh, p->n_slots, p->geo.C, p->geo.SB, p->geo.GW,
@@ -328,7 +336,7 @@ fcc_status_t fcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int 
     if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
     DeviceScope scope(plan->device);
     if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
-    return launch_fp32(plan, static_cast<const float2 *>(d_spectra), T, d_lag_idx, d_peak, d_tau_hat, d_coeffs,
+    return launch_tdoa(plan, static_cast<const float2 *>(d_spectra), T, d_lag_idx, d_peak, d_tau_hat, d_coeffs,
                        d_corr, static_cast<cudaStream_t>(stream));
 }
 
@@ -386,7 +394,7 @@ fcc_status_t fcc_tdoa_host(fcc_plan_t *plan, const void *h_spectra, long long T,
                                      cudaMemcpyHostToDevice, hs));
         FCC_CUDA_TRY(cudaEventRecord(plan->ev[b], hs));
         FCC_CUDA_TRY(cudaStreamWaitEvent(cs, plan->ev[b], 0));
-        fcc_status_t st = launch_fp32(plan, static_cast<const float2 *>(plan->d_stage[b]), n, plan->d_stage_idx[b],
+        fcc_status_t st = launch_tdoa(plan, static_cast<const float2 *>(plan->d_stage[b]), n, plan->d_stage_idx[b],
                                       plan->d_stage_peak[b], h_tau_hat ? plan->d_stage_tau[b] : nullptr, nullptr,
                                       nullptr, cs);
         if (st != FCC_OK) return st;

@@ -89,6 +89,25 @@ struct Fp32Params {
     unsigned *err;
 };
 
+// Kernel parameters of the tensor-core (BF16 / FP16) path.
+struct TcParams {
+    const float2 *spectra;  // [T][M][B]
+    long long T;
+    int M, B, Q, P, n_slots, F, n_tiles;
+    int center, I, KE, KO;
+    float delta;
+    const void *bases;      // 2 parts x [16][2Q] 16-bit, K-major core matrices
+    const float *peq;       // [8]: even bases at bin N/4
+    const float *recon;     // as in Fp32Params
+    const Slot *slots;
+    int *out_idx;
+    float *out_peak;
+    float *out_tau;
+    float *out_coef;
+    float *out_corr;
+    unsigned *err;
+};
+
 }  // namespace fcc
 
 // The plan object behind the opaque ABI handle.
@@ -117,6 +136,11 @@ struct fcc_plan {
     cudaEvent_t ev[6] = {};
     // GCC baseline workspace, created lazily
     void *gcc_state = nullptr;
+    // tensor-core (BF16 / FP16) path
+    void *d_tc_bases = nullptr;
+    float *d_tc_peq = nullptr;
+    int tc_F = 0;
+    size_t tc_smem = 0;
 };
 
 namespace fcc {
@@ -128,6 +152,16 @@ fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, co
 fcc_status_t choose_fp32_geometry(fcc_plan *plan);
 fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,
                          float *peak, float *tau, float *coef, float *corr, cudaStream_t st);
+fcc_status_t prepare_tc(fcc_plan *plan);
+fcc_status_t launch_tc(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                       float *tau, float *coef, float *corr, cudaStream_t st);
+// FP32 or tensor-core path, by the plan's precision.
+inline fcc_status_t launch_tdoa(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                                float *tau, float *coef, float *corr, cudaStream_t st)
+{
+    return plan->info.prec == FCC_PREC_FP32 ? launch_fp32(plan, spectra, T, idx, peak, tau, coef, corr, st)
+                                            : launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
+}
 fcc_status_t gcc_run(fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                      float *corr, cudaStream_t st);
 void gcc_destroy(fcc_plan *plan);

@@ -1,0 +1,629 @@
+// fcc_tc.cu -- the BF16 / FP16 precision forms of the FCC hot path on the
+// 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The projection of Eq. 9 is a dense contraction over the folded bins:
+//   z_e^c[n] = sum_k A_e[row, 2k + c] * pe_n(k),   z_o^c[n] = sum_k A_o[row, 2k + c] * po_n(k),
+// where row is one microphone pair of the tile, c = 0 / 1 the real / imaginary
+// part and A_e = (Re x_s, Im x_s), A_o = (Re x_d, Im x_d) interleaved along k
+// (Eq. 8).  Written as D = A B with B[(k,c), (c',n)] = p_n(k) [c = c'], one
+// tcgen05.mma (M = 128 rows, N = 16 = (c', n), K = 16) per 8 bins and part.
+//
+// Roles in a CTA (persistent over frame tiles of TS = F * slots <= 32 slots):
+//   * 8 producer warps: PHAT of the staged raw frames into FP16 unit-phase
+//     records (FP32 arithmetic; the raw stage is released right after), then
+//     per 32-bin chunk the cross spectra of their 2x2 pair blocks in FP32,
+//     folded and rounded to BF16 / FP16 into the chunk's A tiles (shared
+//     memory, K-major 8x16-byte core matrices; row = q * 32 + slot so that a
+//     quarter-warp's 16-byte stores cover one core matrix);
+//   * 1 MMA warp: allocates TMEM, issues the MMAs of each chunk when its A
+//     tiles are full (FP32 accumulators, two TMEM buffers so that a tile's
+//     epilogue overlaps the next tile's MMAs) and commits them to mbarriers;
+//   * 1 copy warp: streams raw frame tiles with one cp.async.bulk per tile.
+// Epilogue (producer warps 0..3, warp q owns pair q of every slot): tcgen05.ld
+// of the pair's 2K coefficients, the lone bin N/4 added in FP32, then the same
+// FP32 lag-grid reconstruction, argmax and refinement as the FP32 path.
+// Every wait is bounded; TMEM is released on every exit path.
+#include <algorithm>
+#include <cfloat>
+#include <cstdlib>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fcc_device.cuh"
+#include "fcc_internal.h"
+
+namespace fcc {
+namespace {
+
+constexpr int kProdWarps = 8;                 // producer warps (one 4-bin group each)
+constexpr int kThreadsTC = (kProdWarps + 2) * 32;
+constexpr int kChunkRec = 4 * kProdWarps;     // bins per chunk (32)
+constexpr int kChunkCols = 2 * kChunkRec;     // A columns per part per chunk (64)
+constexpr int kPartBytes = 128 * kChunkCols * 2;  // one part of one chunk (16 KB)
+constexpr int kNTile = 16;                    // MMA N: (c', n) with n < 8
+constexpr int kTmemCols = 64;                 // two (even, odd) accumulator buffers
+
+struct TcLayout {
+    size_t bar, slot, bas_e, bas_o, peq, recon, abuf, ubuf, raw, total;
+    int ustride;  // bytes per unit-phase row
+};
+
+__host__ __device__ inline TcLayout tc_layout(int n_slots, int Q, int kh, int center, int rows_tile, int F,
+                                              int frame_bytes)
+{
+    TcLayout L;
+    size_t o = 0;
+    L.bar = o;
+    o += 16 * 8 + 16;  // mbarriers + TMEM address
+    o = (o + 15) & ~(size_t)15;
+    L.slot = o;
+    o += (size_t)n_slots * sizeof(Slot);
+    o = (o + 127) & ~(size_t)127;
+    L.bas_e = o;
+    o += (size_t)kNTile * 2 * Q * 2;
+    L.bas_o = o;
+    o += (size_t)kNTile * 2 * Q * 2;
+    L.peq = o;
+    o += 8 * sizeof(float);
+    o = (o + 15) & ~(size_t)15;
+    L.recon = o;
+    o += (size_t)(center + 1) * 4 * kh * sizeof(float);
+    o = (o + 127) & ~(size_t)127;
+    L.abuf = o;
+    o += 2 * 2 * (size_t)kPartBytes;
+    L.ustride = Q * 8 + 24;  // 8-byte records + lone + pad: rows fall on distinct bank pairs
+    L.ubuf = o;
+    o += (size_t)rows_tile * L.ustride;
+    o = (o + 127) & ~(size_t)127;
+    L.raw = o;
+    o += (((size_t)F * frame_bytes) + 127) & ~(size_t)127;
+    L.total = o;
+    return L;
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle, 8-row x 16-byte core
+// matrices; lbo = byte stride between core matrices along K, sbo = along M/N.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi)
+{
+    if constexpr (PREC == FCC_PREC_BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ float4 rec_f32(uint2 r)
+{
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Barriers (indices into the mbarrier array).
+enum {
+    kFull = 0,     // raw tile landed (tx)
+    kRawEmpty,     // producers done reading the raw tile
+    kUReady,       // unit-phase records written
+    kUFree,        // producers done reading the unit-phase records
+    kAFull0,       // A buffer 0 / 1 written by the producers
+    kAFull1,
+    kAEmpty0,      // MMAs reading A buffer 0 / 1 done (tcgen05.commit)
+    kAEmpty1,
+    kDFull0,       // accumulator buffer 0 / 1 complete (tcgen05.commit)
+    kDFull1,
+    kDEmpty0,      // accumulator buffer 0 / 1 read by the epilogue
+    kDEmpty1,
+    kNumBars
+};
+
+template <int KH, int RS, int PREC>
+__global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int frame_bytes = p.M * p.B * 8;
+    const int rows_tile = p.F * p.M;
+    const TcLayout lay = tc_layout(p.n_slots, p.Q, KH, p.center, rows_tile, p.F, frame_bytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.bar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.bar + kNumBars * 8);
+    Slot *slots = reinterpret_cast<Slot *>(smem + lay.slot);
+    float *peq = reinterpret_cast<float *>(smem + lay.peq);
+    float *recon = reinterpret_cast<float *>(smem + lay.recon);
+    unsigned char *abuf = smem + lay.abuf;
+    unsigned char *ubuf = smem + lay.ubuf;
+    unsigned char *raw = smem + lay.raw;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Q = p.Q, B = p.B, M = p.M;
+    const int nch = Q / kChunkRec;
+    const int n_local = (p.n_tiles > (int)blockIdx.x)
+                            ? (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                            : 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[kFull], 1);
+        mbar_init(&bar[kRawEmpty], kProdWarps);
+        mbar_init(&bar[kUReady], kProdWarps);
+        mbar_init(&bar[kUFree], kProdWarps);
+        mbar_init(&bar[kAFull0], kProdWarps);
+        mbar_init(&bar[kAFull1], kProdWarps);
+        mbar_init(&bar[kAEmpty0], 1);
+        mbar_init(&bar[kAEmpty1], 1);
+        mbar_init(&bar[kDFull0], 1);
+        mbar_init(&bar[kDFull1], 1);
+        mbar_init(&bar[kDEmpty0], 4);
+        mbar_init(&bar[kDEmpty1], 4);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.bases);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + lay.bas_e);
+        const int n16 = 2 * kNTile * 2 * Q * 2 / 16;
+        for (int e = threadIdx.x; e < n16; e += blockDim.x) dst[e] = src[e];
+    }
+    for (int e = threadIdx.x; e < 8; e += blockDim.x) peq[e] = p.peq[e];
+    for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
+    fence_proxy_async();
+    if (warp == kProdWarps) {  // the MMA warp owns the tensor memory
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    auto tile_src = [&](int k, int &nf) {
+        const long long tile = (long long)blockIdx.x + (long long)k * gridDim.x;
+        const long long f0 = tile * p.F;
+        nf = (int)min((long long)p.F, p.T - f0);
+        return f0;
+    };
+
+    if (warp == kProdWarps + 1) {
+        // ================= copy warp =================
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < n_local; ++k) {
+                if (!mbar_wait(&bar[kRawEmpty], ((unsigned)k & 1u) ^ 1u)) {
+                    atomicOr(p.err, kErrTimeout);
+                    break;
+                }
+                int nf;
+                const long long f0 = tile_src(k, nf);
+                const unsigned bytes = (unsigned)nf * (unsigned)frame_bytes;
+                mbar_arrive_expect_tx(&bar[kFull], bytes);
+                bulk_g2s(raw, reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes, bytes,
+                         &bar[kFull]);
+                issued = k + 1;
+            }
+            // never retire with the last bulk copy still in flight
+            if (issued > 0 && !mbar_wait(&bar[kFull], (unsigned)(issued - 1) & 1u)) atomicOr(p.err, kErrTimeout);
+        }
+    } else if (warp == kProdWarps) {
+        // ================= MMA warp =================
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (PREC == FCC_PREC_BF16 ? (1u << 7) | (1u << 10) : 0u) |
+                                   ((uint32_t)(kNTile >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            const uint32_t a_base = smem_u32(abuf);
+            const uint32_t be = smem_u32(smem + lay.bas_e), bo = smem_u32(smem + lay.bas_o);
+            const uint32_t b_sbo = (uint32_t)(2 * Q / 8) * 128;
+            long long cc = 0;  // chunks issued so far
+            bool ok = true;
+            for (int k = 0; k < n_local && ok; ++k) {
+                const int db = k & 1;
+                if (!mbar_wait(&bar[kDEmpty0 + db], ((unsigned)(k >> 1) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d_e = tmem + db * 32, d_o = d_e + 16;
+                for (int ch = 0; ch < nch; ++ch, ++cc) {
+                    const int b = (int)(cc & 1);
+                    if (!mbar_wait(&bar[kAFull0 + b], (unsigned)(cc >> 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ae = a_base + b * 2 * kPartBytes, ao = ae + kPartBytes;
+#pragma unroll
+                    for (int ks = 0; ks < kChunkCols / 16; ++ks) {
+                        const uint32_t koff = ks * 2 * 128;
+                        const uint32_t kb = (uint32_t)(ch * (kChunkCols / 8) + ks * 2) * 128;
+                        const bool acc = (ch > 0) || (ks > 0);
+                        umma_f16(d_e, umma_desc(ae + koff, 128, 1024), umma_desc(be + kb, 128, b_sbo), idesc, acc);
+                        umma_f16(d_o, umma_desc(ao + koff, 128, 1024), umma_desc(bo + kb, 128, b_sbo), idesc, acc);
+                    }
+                    umma_commit(&bar[kAEmpty0 + b]);
+                }
+                if (ok) umma_commit(&bar[kDFull0 + db]);
+            }
+            if (!ok) atomicOr(p.err, kErrTimeout);
+            // retire only when the last MMAs have completed
+            if (cc > 0) {
+                const int b = (int)((cc - 1) & 1);
+                if (!mbar_wait(&bar[kAEmpty0 + b], (unsigned)((cc - 1) >> 1) & 1u)) atomicOr(p.err, kErrTimeout);
+            }
+        }
+    } else {
+        // ================= producer warps =================
+        const int g = warp;         // bin group within a chunk
+        const int sp = lane;        // slot within the tile
+        const int TS = p.F * p.n_slots;
+        const bool live = sp < TS;
+        const int fl = live ? sp / p.n_slots : 0;
+        Slot sl{};
+        if (live) sl = slots[sp - fl * p.n_slots];
+        const unsigned FULLM = 0xffffffffu;
+        long long cc = 0;
+        for (int k = 0; k < n_local; ++k) {
+            int nf;
+            const long long f0 = tile_src(k, nf);
+            const unsigned par = (unsigned)k & 1u;
+            // unit-phase records may be rewritten once the previous tile is done with them
+            if (!mbar_wait(&bar[kUFree], par ^ 1u) || !mbar_wait(&bar[kFull], par)) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+            // ---- PHAT (FP32) into FP16 folded records: row R = (frame, mic)
+            {
+                bool bad = false;
+                for (int R = warp; R < nf * M; R += kProdWarps) {
+                    const float2 *xr = reinterpret_cast<const float2 *>(raw + (size_t)R * B * 8);
+                    uint2 *rec = reinterpret_cast<uint2 *>(ubuf + (size_t)R * lay.ustride);
+#pragma unroll
+                    for (int j = 0; j < RS; ++j) {
+                        const int fp = lane + 32 * j;
+                        if (RS > 1 || fp < Q) {
+                            bool o1, o2;
+                            float2 a = unit_phase_fast(xr[fp], o1);
+                            float2 b = unit_phase_fast(xr[2 * Q - fp], o2);
+                            if (!(o1 && o2)) {
+                                a = unit_phase_slow(xr[fp], bad);
+                                b = unit_phase_slow(xr[2 * Q - fp], bad);
+                            }
+                            const __half2 ha = __floats2half2_rn(a.x, a.y), hb = __floats2half2_rn(b.x, b.y);
+                            rec[fp] = make_uint2(*reinterpret_cast<const uint32_t *>(&ha),
+                                                 *reinterpret_cast<const uint32_t *>(&hb));
+                        }
+                    }
+                    if (lane == 0) {
+                        bool o;
+                        float2 c = unit_phase_fast(xr[Q], o);
+                        if (!o) c = unit_phase_slow(xr[Q], bad);
+                        const __half2 hc = __floats2half2_rn(c.x, c.y);
+                        *reinterpret_cast<__half2 *>(ubuf + (size_t)R * lay.ustride + 8 * Q) = hc;
+                    }
+                }
+                if (__any_sync(FULLM, bad) && lane == 0) atomicOr(p.err, kErrNonFinite);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bar[kRawEmpty]);  // raw tile consumed: the copy warp may refill it
+                mbar_arrive(&bar[kUReady]);
+            }
+            if (!mbar_wait(&bar[kUReady], par)) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+            // ---- A tiles, one 32-bin chunk at a time
+            const int R0 = fl * M;
+            const uint2 *u0 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[0]) * lay.ustride);
+            const uint2 *u1 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[1]) * lay.ustride);
+            const uint2 *u2 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[2]) * lay.ustride);
+            const uint2 *u3 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[3]) * lay.ustride);
+            // the lone bin N/4 of this thread's own pair (q = warp for warps 0..3)
+            float lone_r = 0.f, lone_i = 0.f;
+            if (warp < 4 && live) {
+                const int q = warp;
+                const __half2 hx = *reinterpret_cast<const __half2 *>(
+                    ubuf + (size_t)(R0 + sl.mic[q >> 1]) * lay.ustride + 8 * Q);
+                const __half2 hy = *reinterpret_cast<const __half2 *>(
+                    ubuf + (size_t)(R0 + sl.mic[2 + (q & 1)]) * lay.ustride + 8 * Q);
+                const float2 x = __half22float2(hx), y = __half22float2(hy);
+                lone_r = fmaf(x.x, y.x, x.y * y.y);
+                lone_i = fmaf(x.y, y.x, -(x.x * y.y));
+            }
+            bool ok = true;
+            for (int ch = 0; ch < nch; ++ch, ++cc) {
+                const int b = (int)(cc & 1);
+                if (!mbar_wait(&bar[kAEmpty0 + b], ((unsigned)(cc >> 1) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                uint32_t we[4][4], wo[4][4];  // [pair][bin]: packed (re, im) of x_s / x_d
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int kk = ch * kChunkRec + 4 * g + r;
+                    const float4 X[2] = {rec_f32(u0[kk]), rec_f32(u1[kk])};
+                    const float4 Y[2] = {rec_f32(u2[kk]), rec_f32(u3[kk])};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 x = X[q >> 1], y = Y[q & 1];
+                        const float ar = fmaf(x.x, y.x, x.y * y.y), ai = fmaf(x.y, y.x, -(x.x * y.y));
+                        const float br = fmaf(x.z, y.z, x.w * y.w), bi = fmaf(x.w, y.z, -(x.z * y.w));
+                        we[q][r] = pack16<PREC>(ar + br, ai + bi);  // x_s (Eq. 8)
+                        wo[q][r] = pack16<PREC>(ar - br, ai - bi);  // x_d
+                    }
+                }
+                unsigned char *ae = abuf + b * 2 * kPartBytes, *ao = ae + kPartBytes;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = 32 * q + sp;
+                    const int off = ((row >> 3) * (kChunkCols / 8) + g) * 128 + (row & 7) * 16;
+                    const uint4 ve = live ? make_uint4(we[q][0], we[q][1], we[q][2], we[q][3]) : make_uint4(0, 0, 0, 0);
+                    const uint4 vo = live ? make_uint4(wo[q][0], wo[q][1], wo[q][2], wo[q][3]) : make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4 *>(ae + off) = ve;
+                    *reinterpret_cast<uint4 *>(ao + off) = vo;
+                }
+                fence_proxy_async();  // generic-proxy stores -> tensor-core reads
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[kAFull0 + b]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[kUFree]);
+            if (!ok) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+            // ---- epilogue: warps 0..3, thread = pair q = warp of slot sp
+            if (warp < 4) {
+                const int db = k & 1;
+                if (!mbar_wait(&bar[kDFull0 + db], (unsigned)(k >> 1) & 1u)) {
+                    if (lane == 0) atomicOr(p.err, kErrTimeout);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float de[16], dd[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + db * 32;
+                tmem_ld16(taddr, de);
+                tmem_ld16(taddr + 16, dd);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar[kDEmpty0 + db]);
+                const int q = warp;
+                const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
+                if (live && fl < nf && pq >= 0) {
+                    f2 zE[KH], zO[KH];
+#pragma unroll
+                    for (int v = 0; v < KH; ++v) {
+                        zE[v] = pk(fmaf(peq[v], lone_r, de[v]), fmaf(peq[v], lone_i, de[8 + v]));
+                        zO[v] = pk(dd[v], dd[8 + v]);
+                    }
+                    const size_t o = (size_t)(f0 + fl) * p.P + pq;
+                    float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
+                    float S, D;
+                    eval_SD<KH>(recon, 0, zE, zO, S, D);
+                    float best = S - D;
+                    int bi = p.center;
+                    if (corr) corr[p.center] = best;
+                    for (int m = 1; m <= p.center; ++m) {
+                        eval_SD<KH>(recon, m, zE, zO, S, D);
+                        const float ym = S + D, yp = S - D;
+                        if (ym >= best) {
+                            best = ym;
+                            bi = p.center - m;
+                        }
+                        if (yp > best) {
+                            best = yp;
+                            bi = p.center + m;
+                        }
+                        if (corr) {
+                            corr[p.center - m] = ym;
+                            corr[p.center + m] = yp;
+                        }
+                    }
+                    p.out_idx[o] = bi;
+                    p.out_peak[o] = best;
+                    if (p.out_tau) {
+                        float off = 0.f;
+                        if (bi > 0 && bi < p.I - 1) {
+                            const double y_m = y_at<KH>(recon, p.center, bi - 1, zE, zO);
+                            const double y_p = y_at<KH>(recon, p.center, bi + 1, zE, zO);
+                            const double num = y_m - y_p;
+                            const double den = (y_m - 2.0 * (double)best) + y_p;
+                            if (den < 0.0) off = fminf(0.5f, fmaxf(-0.5f, 0.5f * (float)num / (float)den));
+                        }
+                        p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
+                    }
+                    if (p.out_coef) {
+                        const int K = p.KE + p.KO;
+                        float *cf = p.out_coef + o * 2 * K;
+#pragma unroll
+                        for (int v = 0; v < KH; ++v) {
+                            float a, b2;
+                            if (v < p.KE) {
+                                upk(zE[v], a, b2);
+                                cf[v] = a;
+                                cf[p.KE + v] = b2;
+                            }
+                            if (v < p.KO) {
+                                upk(zO[v], a, b2);
+                                cf[2 * p.KE + v] = a;
+                                cf[2 * p.KE + p.KO + v] = b2;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == kProdWarps)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols));
+}
+
+template <int KH, int RS, int PREC>
+fcc_status_t launch_tc_inst(const fcc_plan *plan, const TcParams &prm, cudaStream_t st, int grid)
+{
+    static bool attr_set[64] = {};
+    const int dev = plan->device;
+    if (!attr_set[dev & 63]) {
+        cudaError_t e = cudaFuncSetAttribute(fcc_tc_kernel<KH, RS, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             232448);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fcc_tc_kernel)");
+        attr_set[dev & 63] = true;
+    }
+    fcc_tc_kernel<KH, RS, PREC><<<grid, kThreadsTC, plan->tc_smem, st>>>(prm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fcc_tc_kernel launch");
+    return FCC_OK;
+}
+
+template <int KH, int PREC>
+fcc_status_t launch_tc_kh(const fcc_plan *plan, const TcParams &prm, cudaStream_t st, int grid)
+{
+    switch (prm.Q / 32) {
+    case 1: return launch_tc_inst<KH, 1, PREC>(plan, prm, st, grid);
+    case 2: return launch_tc_inst<KH, 2, PREC>(plan, prm, st, grid);
+    case 4: return launch_tc_inst<KH, 4, PREC>(plan, prm, st, grid);
+    case 8: return launch_tc_inst<KH, 8, PREC>(plan, prm, st, grid);
+    default: return fail(FCC_ERR_UNSUPPORTED, "the tensor-core path needs 128 <= N <= 1024");
+    }
+}
+
+template <int PREC>
+fcc_status_t launch_tc_prec(const fcc_plan *plan, const TcParams &prm, cudaStream_t st, int grid)
+{
+    switch (plan->kh) {
+    case 2: return launch_tc_kh<2, PREC>(plan, prm, st, grid);
+    case 4: return launch_tc_kh<4, PREC>(plan, prm, st, grid);
+    case 6: return launch_tc_kh<6, PREC>(plan, prm, st, grid);
+    case 8: return launch_tc_kh<8, PREC>(plan, prm, st, grid);
+    default: return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    }
+}
+
+}  // namespace
+
+// Host side: check the tensor-core path applies and size its shared memory;
+// pack the basis tiles (K-major core matrices, rows (c', n), columns (k, c)).
+fcc_status_t prepare_tc(fcc_plan *plan)
+{
+    const fcc_plan_info_t &in = plan->info;
+    if (in.Q % kChunkRec != 0 || in.Q > 256)
+        return fail(FCC_ERR_UNSUPPORTED, "the tensor-core path needs 128 <= N <= 1024");
+    if (plan->n_slots > 32) return fail(FCC_ERR_UNSUPPORTED, "the tensor-core path needs M <= 16");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    const int frame_bytes = in.M * in.B * 8;
+    if (frame_bytes % 16) return fail(FCC_ERR_UNSUPPORTED, "the tensor-core path needs an even number of mics");
+    int smem_max = 0;
+    FCC_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
+    smem_max = std::min(smem_max, 232448);
+    int F = std::max(1, 32 / plan->n_slots);
+    TcLayout L{};
+    for (; F >= 1; --F) {
+        L = tc_layout(plan->n_slots, in.Q, plan->kh, in.center, F * in.M, F, frame_bytes);
+        if (L.total <= (size_t)smem_max) break;
+    }
+    if (F < 1) return fail(FCC_ERR_UNSUPPORTED, "frame too large for the tensor-core path");
+    plan->tc_F = F;
+    plan->tc_smem = L.total;
+    // basis tiles, BF16 or FP16
+    const int Q = in.Q, KB = 2 * Q;  // columns (k, c), k < Q
+    std::vector<uint16_t> tiles((size_t)2 * kNTile * KB, 0);
+    auto put = [&](int part, int n, int kc, double v) {
+        const size_t off = (size_t)part * kNTile * KB +
+                           (((size_t)(n / 8) * (KB / 8) + kc / 8) * 64 + (n % 8) * 8 + (kc % 8));
+        if (in.prec == FCC_PREC_BF16) {
+            __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+            tiles[off] = *reinterpret_cast<uint16_t *>(&h);
+        } else {
+            __half h = __float2half_rn((float)v);
+            tiles[off] = *reinterpret_cast<uint16_t *>(&h);
+        }
+    };
+    for (int c = 0; c < 2; ++c)
+        for (int nb = 0; nb < 8; ++nb)
+            for (int k = 0; k < Q; ++k) {
+                const int n = c * 8 + nb, kc = 2 * k + c;
+                put(0, n, kc, nb < in.K_even ? plan->Pe[(size_t)nb * (Q + 1) + k] : 0.0);
+                put(1, n, kc, nb < in.K_odd ? plan->Po[(size_t)nb * Q + k] : 0.0);
+            }
+    std::vector<float> peq(8, 0.f);
+    for (int nb = 0; nb < in.K_even && nb < 8; ++nb) peq[nb] = (float)plan->Pe[(size_t)nb * (Q + 1) + Q];
+    FCC_CUDA_TRY(cudaMalloc(&plan->d_tc_bases, tiles.size() * sizeof(uint16_t)));
+    FCC_CUDA_TRY(cudaMemcpy(plan->d_tc_bases, tiles.data(), tiles.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    FCC_CUDA_TRY(cudaMalloc(&plan->d_tc_peq, 8 * sizeof(float)));
+    FCC_CUDA_TRY(cudaMemcpy(plan->d_tc_peq, peq.data(), 8 * sizeof(float), cudaMemcpyHostToDevice));
+    return FCC_OK;
+}
+
+fcc_status_t launch_tc(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak, float *tau,
+                       float *coef, float *corr, cudaStream_t st)
+{
+    const fcc_plan_info_t &in = plan->info;
+    if (!plan->tc_smem) return fail(FCC_ERR_UNSUPPORTED, "the tensor-core path is not available for this plan");
+    if (reinterpret_cast<uintptr_t>(spectra) & 15) return fail(FCC_ERR_INVALID_ARG, "spectra not 16-byte aligned");
+    TcParams prm{};
+    prm.spectra = spectra;
+    prm.T = T;
+    prm.M = in.M;
+    prm.B = in.B;
+    prm.Q = in.Q;
+    prm.P = in.P;
+    prm.n_slots = plan->n_slots;
+    prm.F = plan->tc_F;
+    const long long n_tiles = (T + prm.F - 1) / prm.F;
+    if (n_tiles > 0x7fffffffLL) return fail(FCC_ERR_UNSUPPORTED, "too many frames for one call");
+    prm.n_tiles = (int)n_tiles;
+    prm.center = in.center;
+    prm.I = in.I;
+    prm.KE = in.K_even;
+    prm.KO = in.K_odd;
+    prm.delta = (float)in.delta;
+    prm.bases = plan->d_tc_bases;
+    prm.peq = plan->d_tc_peq;
+    prm.recon = plan->d_recon;
+    prm.slots = plan->d_slots;
+    prm.out_idx = idx;
+    prm.out_peak = peak;
+    prm.out_tau = tau;
+    prm.out_coef = coef;
+    prm.out_corr = corr;
+    prm.err = plan->d_err;
+    const int grid = (int)std::min<long long>(n_tiles, (long long)plan->num_sms);
+    if (in.prec == FCC_PREC_BF16) return launch_tc_prec<FCC_PREC_BF16>(plan, prm, st, grid);
+    return launch_tc_prec<FCC_PREC_FP16>(plan, prm, st, grid);
+}
+
+}  // namespace fcc
