@@ -322,3 +322,126 @@ int or_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Learned TDoA head (not part of the paper's method; an extension that maps a
+ * pair-frame's 2K projection coefficients to a sub-sample TDoA and a
+ * confidence).  Plain FP64 definitions, one sample at a time:
+ *   a1 = W1 x + b1,  h1 = gelu(a1)           (H x nin, exact erf GELU)
+ *   a2 = W2 h1 + b2, h2 = gelu(a2)           (H x H)
+ *   y  = W3 h2 + b3                          (2 x H): y0 = TDoA, y1 = confidence logit
+ * Loss (mean over n): (y0 - t)^2 + lambda * BCE(sigmoid(y1), g) with the
+ * target g = [|y0 - t| <= |t_fcc - t|] (held constant).  Parameters are packed
+ * as W1, b1, W2, b2, W3, b3 (row-major).
+ * ------------------------------------------------------------------------ */
+static double or_gelu(double a) { return 0.5 * a * (1.0 + erf(a / sqrt(2.0))); }
+static double or_gelu_d(double a)
+{
+    return 0.5 * (1.0 + erf(a / sqrt(2.0))) + a * exp(-0.5 * a * a) / sqrt(2.0 * OR_PI);
+}
+
+long long or_mlp_nparams(int nin, int H) { return (long long)H * nin + H + (long long)H * H + H + 2 * H + 2; }
+
+static void or_mlp_unpack(const double *p, int nin, int H, const double **W1, const double **b1,
+                          const double **W2, const double **b2, const double **W3, const double **b3)
+{
+    *W1 = p;
+    *b1 = *W1 + (size_t)H * nin;
+    *W2 = *b1 + H;
+    *b2 = *W2 + (size_t)H * H;
+    *W3 = *b2 + H;
+    *b3 = *W3 + 2 * (size_t)H;
+}
+
+static void or_mlp_one(const double *x, int nin, int H, const double *params, double *a1, double *a2, double *y)
+{
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    or_mlp_unpack(params, nin, H, &W1, &b1, &W2, &b2, &W3, &b3);
+    for (int j = 0; j < H; ++j) {
+        double s = b1[j];
+        for (int i = 0; i < nin; ++i) s += W1[(size_t)j * nin + i] * x[i];
+        a1[j] = s;
+    }
+    for (int j = 0; j < H; ++j) {
+        double s = b2[j];
+        for (int i = 0; i < H; ++i) s += W2[(size_t)j * H + i] * or_gelu(a1[i]);
+        a2[j] = s;
+    }
+    for (int o = 0; o < 2; ++o) {
+        double s = b3[o];
+        for (int j = 0; j < H; ++j) s += W3[(size_t)o * H + j] * or_gelu(a2[j]);
+        y[o] = s;
+    }
+}
+
+void or_mlp_forward(const double *x, long long n, int nin, int H, const double *params, double *y)
+{
+    double *a1 = (double *)malloc(sizeof(double) * H), *a2 = (double *)malloc(sizeof(double) * H);
+    for (long long s = 0; s < n; ++s) or_mlp_one(x + (size_t)s * nin, nin, H, params, a1, a2, y + 2 * s);
+    free(a1);
+    free(a2);
+}
+
+/* Mean loss; grad (same packing as params) is overwritten with dLoss/dparams. */
+double or_mlp_loss_grad(const double *x, long long n, int nin, int H, const double *params, const double *t,
+                        const double *tfcc, double lambda, double *grad)
+{
+    const double *W1, *b1, *W2, *b2, *W3, *b3;
+    or_mlp_unpack(params, nin, H, &W1, &b1, &W2, &b2, &W3, &b3);
+    const long long np_ = or_mlp_nparams(nin, H);
+    for (long long k = 0; k < np_; ++k) grad[k] = 0.0;
+    double *gW1 = grad, *gb1 = gW1 + (size_t)H * nin, *gW2 = gb1 + H, *gb2 = gW2 + (size_t)H * H, *gW3 = gb2 + H,
+           *gb3 = gW3 + 2 * (size_t)H;
+    double *a1 = (double *)malloc(sizeof(double) * H), *a2 = (double *)malloc(sizeof(double) * H);
+    double *d2 = (double *)malloc(sizeof(double) * H), *d1 = (double *)malloc(sizeof(double) * H);
+    double loss = 0.0;
+    for (long long s = 0; s < n; ++s) {
+        const double *xs = x + (size_t)s * nin;
+        double y[2];
+        or_mlp_one(xs, nin, H, params, a1, a2, y);
+        const double e = y[0] - t[s];
+        const double g = fabs(e) <= fabs(tfcc[s] - t[s]) ? 1.0 : 0.0;
+        const double c = 1.0 / (1.0 + exp(-y[1]));
+        /* BCE(sigmoid(y1), g) = softplus(y1) - g y1, written stably */
+        const double bce = (y[1] > 0 ? y[1] + log1p(exp(-y[1])) : log1p(exp(y[1]))) - g * y[1];
+        loss += e * e + lambda * bce;
+        const double dy0 = 2.0 * e / (double)n, dy1 = lambda * (c - g) / (double)n;
+        for (int j = 0; j < H; ++j) {
+            const double h2 = or_gelu(a2[j]);
+            gW3[j] += dy0 * h2;
+            gW3[H + j] += dy1 * h2;
+            d2[j] = (W3[j] * dy0 + W3[H + j] * dy1) * or_gelu_d(a2[j]);
+            gb2[j] += d2[j];
+        }
+        gb3[0] += dy0;
+        gb3[1] += dy1;
+        for (int i = 0; i < H; ++i) {
+            const double h1 = or_gelu(a1[i]);
+            double s2 = 0.0;
+            for (int j = 0; j < H; ++j) {
+                gW2[(size_t)j * H + i] += d2[j] * h1;
+                s2 += W2[(size_t)j * H + i] * d2[j];
+            }
+            d1[i] = s2 * or_gelu_d(a1[i]);
+            gb1[i] += d1[i];
+            for (int k = 0; k < nin; ++k) gW1[(size_t)i * nin + k] += d1[i] * xs[k];
+        }
+    }
+    free(a1);
+    free(a2);
+    free(d1);
+    free(d2);
+    return loss / (double)n;
+}
+
+/* Adam (Kingma & Ba 2015) with bias correction; step counts from 1. */
+void or_adam(double *p, const double *g, double *m, double *v, long long n, int step, double lr, double beta1,
+             double beta2, double eps)
+{
+    const double c1 = 1.0 - pow(beta1, step), c2 = 1.0 - pow(beta2, step);
+    for (long long k = 0; k < n; ++k) {
+        m[k] = beta1 * m[k] + (1.0 - beta1) * g[k];
+        v[k] = beta2 * v[k] + (1.0 - beta2) * g[k] * g[k];
+        p[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
+}

@@ -76,6 +76,16 @@ def _load():
                                     ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _ip, _dp, _dp,
                                     _dp, ctypes.c_int]
             lib.or_tdoa.restype = None
+            lib.or_mlp_nparams.argtypes = [ctypes.c_int, ctypes.c_int]
+            lib.or_mlp_nparams.restype = ctypes.c_longlong
+            lib.or_mlp_forward.argtypes = [_dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _dp, _dp]
+            lib.or_mlp_forward.restype = None
+            lib.or_mlp_loss_grad.argtypes = [_dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                             ctypes.c_double, _dp]
+            lib.or_mlp_loss_grad.restype = ctypes.c_double
+            lib.or_adam.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            lib.or_adam.restype = None
             lib.or_max_threads.argtypes = []
             lib.or_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -220,3 +230,43 @@ def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: b
                     idx.ctypes.data_as(_ip), _d(peak), _d(tau),
                     _d(y) if want_y else None, nt)
     return idx, peak, tau, y
+
+
+# ----------------------------------------------------------------------------
+# learned TDoA head (not in the paper): FP64 reference of the MLP
+# ----------------------------------------------------------------------------
+def mlp_nparams(nin: int, H: int) -> int:
+    return int(_load().or_mlp_nparams(nin, H))
+
+
+def mlp_forward(x, params, nin: int, H: int) -> np.ndarray:
+    """y [n, 2] = W3 gelu(W2 gelu(W1 x + b1) + b2) + b3 (exact erf GELU)."""
+    x = np.ascontiguousarray(x, np.float64)
+    params = np.ascontiguousarray(params, np.float64)
+    y = np.empty((x.shape[0], 2))
+    _load().or_mlp_forward(_d(x), x.shape[0], nin, H, _d(params), _d(y))
+    return y
+
+
+def mlp_loss_grad(x, params, t, tfcc, nin: int, H: int, lam: float):
+    """Mean of (y0 - t)^2 + lam * BCE(sigmoid(y1), [|y0 - t| <= |tfcc - t|]) and its gradient."""
+    x = np.ascontiguousarray(x, np.float64)
+    params = np.ascontiguousarray(params, np.float64)
+    t = np.ascontiguousarray(t, np.float64)
+    tfcc = np.ascontiguousarray(tfcc, np.float64)
+    g = np.empty_like(params)
+    loss = _load().or_mlp_loss_grad(_d(x), x.shape[0], nin, H, _d(params), _d(t), _d(tfcc), lam, _d(g))
+    return float(loss), g
+
+
+def adam(params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam update of params, m, v (float64 arrays)."""
+    _load().or_adam(_d(params), _d(np.ascontiguousarray(grad, np.float64)), _d(m), _d(v), len(params), step, lr,
+                    beta1, beta2, eps)
+
+
+def round_bf16(a) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
