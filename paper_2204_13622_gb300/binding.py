@@ -23,7 +23,10 @@ PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 # every symbol include/fcc.h declares
 EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_taus",
            "fcc_plan_singular_values", "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa",
-           "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc"]
+           "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc",
+           # include/fcc_mlp.h
+           "fcc_mlp_num_params", "fcc_mlp_create", "fcc_mlp_destroy", "fcc_mlp_get_state",
+           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -77,6 +80,21 @@ def lib():
         L.fcc_status_string.restype = ctypes.c_char_p
         L.fcc_last_error.argtypes = []
         L.fcc_last_error.restype = ctypes.c_char_p
+        _fp = ctypes.POINTER(ctypes.c_float)
+        L.fcc_mlp_num_params.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.fcc_mlp_num_params.restype = ctypes.c_longlong
+        L.fcc_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, _fp, ctypes.c_double, _fp,
+                                     ctypes.c_int, ctypes.POINTER(_vp)]
+        L.fcc_mlp_destroy.argtypes = [_vp]
+        L.fcc_mlp_destroy.restype = None
+        L.fcc_mlp_get_state.argtypes = [_vp, _fp, _fp, _fp, ctypes.POINTER(ctypes.c_longlong)]
+        L.fcc_mlp_set_state.argtypes = [_vp, _fp, _fp, _fp, ctypes.c_longlong]
+        L.fcc_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
+        L.fcc_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp]
+        L.fcc_mlp_infer.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp, _vp, _vp]
+        for name in ("fcc_mlp_create", "fcc_mlp_get_state", "fcc_mlp_set_state", "fcc_mlp_gradient",
+                     "fcc_mlp_train_step", "fcc_mlp_infer"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_plan_create", "fcc_plan_info", "fcc_plan_taus", "fcc_plan_singular_values",
                      "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa", "fcc_plan_sync",
                      "fcc_plan_bases_noalloc"):
@@ -250,3 +268,91 @@ def plan_bases_noalloc(n_mics: int, fs: float, N: int, lag_den: int, tau_max: fl
                                        Ue.ctypes.data_as(_dp), Uo.ctypes.data_as(_dp), st),
           "fcc_plan_bases_noalloc")
     return {k: getattr(info, k) for k, _ in PlanInfo._fields_}, se, so, Pe, Po, Ue, Uo
+
+
+_fptr = ctypes.POINTER(ctypes.c_float)
+
+
+class MLP:
+    """The learned TDoA head (include/fcc_mlp.h): 2K -> 128 -> 128 -> 2 with BF16
+    weights and FP32 masters, trained by the library's own kernels."""
+
+    HIDDEN = 128
+
+    def __init__(self, n_in: int, params: np.ndarray, in_scale=None, conf_weight: float = 0.1,
+                 device: int | None = None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device, self.n_in = int(device), int(n_in)
+        self.n_params = int(lib().fcc_mlp_num_params(self.n_in, self.HIDDEN))
+        p = np.ascontiguousarray(params, np.float32).ravel()
+        if p.size != self.n_params:
+            raise ValueError(f"params must hold {self.n_params} floats")
+        sc = None
+        if in_scale is not None:
+            sc = np.ascontiguousarray(np.broadcast_to(np.asarray(in_scale, np.float32), (self.n_in,)))
+        h = _vp()
+        check(lib().fcc_mlp_create(self.n_in, self.HIDDEN, None if sc is None else sc.ctypes.data_as(_fptr),
+                                   float(conf_weight), p.ctypes.data_as(_fptr), self.device, ctypes.byref(h)),
+              "fcc_mlp_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fcc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_state(self):
+        p, m, v = (np.empty(self.n_params, np.float32) for _ in range(3))
+        step = ctypes.c_longlong()
+        check(lib().fcc_mlp_get_state(self._h, p.ctypes.data_as(_fptr), m.ctypes.data_as(_fptr),
+                                      v.ctypes.data_as(_fptr), ctypes.byref(step)), "fcc_mlp_get_state")
+        return p, m, v, step.value
+
+    def set_state(self, params, m=None, v=None, step: int = 0):
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float32).ravel() for a in (params, m, v)]
+        ptrs = [None if a is None else a.ctypes.data_as(_fptr) for a in arrs]
+        check(lib().fcc_mlp_set_state(self._h, *ptrs, int(step)), "fcc_mlp_set_state")
+
+    def _check(self, feat, *vecs):
+        import torch
+        if feat.dtype != torch.float32 or feat.dim() != 2 or feat.shape[1] != self.n_in or not feat.is_contiguous():
+            raise ValueError(f"features must be contiguous float32 [n, {self.n_in}]")
+        for v in vecs:
+            if v is not None and (v.dtype != torch.float32 or v.numel() != feat.shape[0] or not v.is_contiguous()):
+                raise ValueError("per-sample vectors must be contiguous float32 [n]")
+
+    def gradient(self, feat, tau_true, tau_fcc, stream=None):
+        """(grad [n_params], mean loss) as device tensors."""
+        import torch
+        self._check(feat, tau_true, tau_fcc)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        check(lib().fcc_mlp_gradient(self._h, _ptr(feat), _ptr(tau_true), _ptr(tau_fcc), feat.shape[0], _ptr(g),
+                                     _ptr(loss), _stream(stream, feat.device)), "fcc_mlp_gradient")
+        return g, loss
+
+    def train_step(self, feat, tau_true, tau_fcc, lr: float, loss=None, stream=None):
+        """One Adam step; the batch loss (before the update) goes to `loss` if given."""
+        self._check(feat, tau_true, tau_fcc)
+        check(lib().fcc_mlp_train_step(self._h, _ptr(feat), _ptr(tau_true), _ptr(tau_fcc), feat.shape[0],
+                                       float(lr), _ptr(loss), _stream(stream, feat.device)), "fcc_mlp_train_step")
+
+    def infer(self, feat, tau_fcc=None, threshold: float = 0.5, stream=None, out=None):
+        """dict(tau, conf, raw) of device tensors [n]."""
+        import torch
+        self._check(feat, tau_fcc)
+        n = feat.shape[0]
+        if out is None:
+            out = {k: torch.empty(n, dtype=torch.float32, device=feat.device) for k in ("tau", "conf", "raw")}
+        check(lib().fcc_mlp_infer(self._h, _ptr(feat), _ptr(tau_fcc), n, float(threshold), _ptr(out["tau"]),
+                                  _ptr(out.get("conf")), _ptr(out.get("raw")), _stream(stream, feat.device)),
+              "fcc_mlp_infer")
+        return out

@@ -1,0 +1,536 @@
+// fcc_mlp.cu -- the learned TDoA head (an extension; the paper has no learned
+// part): a 2K -> 128 -> 128 -> 2 MLP on a pair-frame's projection coefficients,
+// y0 = sub-sample TDoA, y1 = confidence logit, exact erf GELU, BF16 weights,
+// FP32 accumulation and FP32 master weights for training.
+//
+// Kernels (hand-written, CUDA cores; one block = 128 threads, thread j <-> hidden
+// unit j, tiles of 32 samples):
+//   mlp_grad_kernel   persistent blocks; per tile: forward (keeping gelu and
+//                     gelu' of both layers in shared memory), loss gradient,
+//                     backward; parameter gradients accumulate per block and are
+//                     written once per block;
+//   mlp_reduce_kernel sums the per-block partials in a fixed order (bitwise
+//                     reproducible gradients);
+//   mlp_adam_kernel   Adam on the FP32 masters, refreshing the BF16 copies;
+//   mlp_infer_kernel  forward + confidence gate: TDoA = y0 when sigmoid(y1) >=
+//                     threshold, else the plain FCC estimate.
+// Loss (mean over the batch): (y0 - t)^2 + lambda * BCE(sigmoid(y1), g), with the
+// target g = [|y0 - t| <= |t_fcc - t|]: the confidence learns when the network
+// beats the plain argmax + parabola.
+#include <algorithm>
+#include <cmath>
+#include <cuda_bf16.h>
+#include <new>
+#include <vector>
+
+#include "fcc_internal.h"
+#include "fcc_mlp.h"
+
+namespace fcc {
+namespace {
+
+constexpr int kH = 128;      // hidden width
+constexpr int kTileS = 32;   // samples per tile
+constexpr int kMaxIn = 32;   // 2K <= 32
+constexpr int kLd = kH + 1;  // padded row of the activation tiles
+
+__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float a)
+{
+    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
+}
+
+struct MlpW {
+    const __nv_bfloat16 *W1, *W2, *W3;  // BF16 copies: [H][nin], [H][H], [2][H]
+    const float *b1, *b2, *b3;          // FP32
+    const float *scale;                 // per-input scale [nin]
+    int nin;
+};
+
+// Shared-memory image of the weights (W2 also transposed for the backward).
+struct MlpSmem {
+    __nv_bfloat16 W2[kH * kH];
+    __nv_bfloat16 W2T[kH * kH];
+    __nv_bfloat16 W1[kH * kMaxIn];
+    __nv_bfloat16 W3[2 * kH];
+    float b1[kH], b2[kH], b3[2];
+    float scale[kMaxIn];
+    float X[kTileS][kMaxIn + 1];
+    float H1[kTileS][kLd], G1[kTileS][kLd];  // gelu(a1), gelu'(a1)
+    float H2[kTileS][kLd], G2[kTileS][kLd];  // gelu(a2), gelu'(a2) -> reused for da2
+    float Y[kTileS][2], DY[kTileS][2];
+};
+
+__device__ void load_weights(MlpSmem &s, const MlpW &w)
+{
+    for (int e = threadIdx.x; e < kH * kH; e += blockDim.x) {
+        const __nv_bfloat16 v = w.W2[e];
+        s.W2[e] = v;
+        s.W2T[(e % kH) * kH + e / kH] = v;
+    }
+    for (int e = threadIdx.x; e < kH * w.nin; e += blockDim.x) s.W1[e] = w.W1[e];
+    for (int e = threadIdx.x; e < 2 * kH; e += blockDim.x) s.W3[e] = w.W3[e];
+    for (int e = threadIdx.x; e < kH; e += blockDim.x) {
+        s.b1[e] = w.b1[e];
+        s.b2[e] = w.b2[e];
+    }
+    if (threadIdx.x < 2) s.b3[threadIdx.x] = w.b3[threadIdx.x];
+    if (threadIdx.x < kMaxIn) s.scale[threadIdx.x] = threadIdx.x < w.nin ? w.scale[threadIdx.x] : 0.f;
+}
+
+// Forward of one tile of ns <= 32 samples (rows >= ns are zero).  Needs
+// s.X loaded; leaves H1, G1, H2, G2, Y in shared memory.
+__device__ void forward_tile(MlpSmem &s, int nin, bool want_grad)
+{
+    const int j = threadIdx.x;
+    {
+        float w[kMaxIn];
+#pragma unroll
+        for (int i = 0; i < kMaxIn; ++i) w[i] = i < nin ? __bfloat162float(s.W1[j * nin + i]) : 0.f;
+        for (int r = 0; r < kTileS; ++r) {
+            float a = s.b1[j];
+#pragma unroll
+            for (int i = 0; i < kMaxIn; ++i) a = fmaf(w[i], s.X[r][i], a);
+            s.H1[r][j] = gelu(a);
+            if (want_grad) s.G1[r][j] = gelu_d(a);
+        }
+    }
+    __syncthreads();
+    {
+        float acc[kTileS];
+#pragma unroll
+        for (int r = 0; r < kTileS; ++r) acc[r] = s.b2[j];
+        for (int i = 0; i < kH; ++i) {
+            const float w = __bfloat162float(s.W2T[i * kH + j]);
+#pragma unroll
+            for (int r = 0; r < kTileS; ++r) acc[r] = fmaf(w, s.H1[r][i], acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kTileS; ++r) {
+            s.H2[r][j] = gelu(acc[r]);
+            if (want_grad) s.G2[r][j] = gelu_d(acc[r]);
+        }
+    }
+    __syncthreads();
+    if (j < 2 * kTileS) {
+        const int r = j >> 1, o = j & 1;
+        float y = s.b3[o];
+        for (int i = 0; i < kH; ++i) y = fmaf(__bfloat162float(s.W3[o * kH + i]), s.H2[r][i], y);
+        s.Y[r][o] = y;
+    }
+    __syncthreads();
+}
+
+__device__ void load_x(MlpSmem &s, const float *feat, long long base, int ns, int nin)
+{
+    for (int e = threadIdx.x; e < kTileS * kMaxIn; e += blockDim.x) {
+        const int r = e / kMaxIn, i = e % kMaxIn;
+        s.X[r][i] = (r < ns && i < nin) ? feat[(size_t)(base + r) * nin + i] * s.scale[i] : 0.f;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kH) mlp_grad_kernel(MlpW w, const float *feat, const float *tau_true,
+                                                      const float *tau_fcc, long long n, float lambda,
+                                                      float *partial, long long n_params, float *loss_partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
+    const int nin = w.nin, j = threadIdx.x;
+    load_weights(s, w);
+    __syncthreads();
+    float gW1[kMaxIn], gb1 = 0.f, gb2 = 0.f, gW3_0 = 0.f, gW3_1 = 0.f, gb3_0 = 0.f, gb3_1 = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMaxIn; ++i) gW1[i] = 0.f;
+    float *gW2 = reinterpret_cast<float *>(smem_raw + sizeof(MlpSmem));  // [H][kLd], row j owned by thread j
+    for (int i = 0; i < kH; ++i) gW2[j * kLd + i] = 0.f;
+    const float inv_n = 1.f / (float)n;
+    const long long n_tiles = (n + kTileS - 1) / kTileS;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const long long base = t * kTileS;
+        const int ns = (int)min((long long)kTileS, n - base);
+        load_x(s, feat, base, ns, nin);
+        forward_tile(s, nin, true);
+        // loss gradient at the outputs
+        if (j < kTileS) {
+            float dy0 = 0.f, dy1 = 0.f;
+            if (j < ns) {
+                const float y0 = s.Y[j][0], y1 = s.Y[j][1];
+                const float tt = tau_true[base + j], tf = tau_fcc[base + j];
+                const float e = y0 - tt;
+                const float g = fabsf(e) <= fabsf(tf - tt) ? 1.f : 0.f;
+                const float c = 1.f / (1.f + expf(-y1));
+                const float bce = (y1 > 0.f ? y1 + log1pf(expf(-y1)) : log1pf(expf(y1))) - g * y1;
+                lsum += e * e + lambda * bce;
+                dy0 = 2.f * e * inv_n;
+                dy1 = lambda * (c - g) * inv_n;
+            }
+            s.DY[j][0] = dy0;
+            s.DY[j][1] = dy1;
+        }
+        __syncthreads();
+        // layer 3 and da2 = (W3^T dy) * gelu'(a2)
+        {
+            const float w30 = __bfloat162float(s.W3[j]), w31 = __bfloat162float(s.W3[kH + j]);
+            for (int r = 0; r < kTileS; ++r) {
+                const float dy0 = s.DY[r][0], dy1 = s.DY[r][1];
+                gW3_0 = fmaf(dy0, s.H2[r][j], gW3_0);
+                gW3_1 = fmaf(dy1, s.H2[r][j], gW3_1);
+                const float da2 = fmaf(w30, dy0, w31 * dy1) * s.G2[r][j];
+                s.G2[r][j] = da2;
+                gb2 += da2;
+            }
+            if (j == 0)
+                for (int r = 0; r < kTileS; ++r) {
+                    gb3_0 += s.DY[r][0];
+                    gb3_1 += s.DY[r][1];
+                }
+        }
+        __syncthreads();
+        // dW2[j][i] += sum_r da2[r][j] h1[r][i];  dh1[r][i] = sum_j W2[j][i] da2[r][j]
+        {
+            float d2[kTileS];
+#pragma unroll
+            for (int r = 0; r < kTileS; ++r) d2[r] = s.G2[r][j];
+            for (int i = 0; i < kH; ++i) {
+                float acc = 0.f;
+#pragma unroll
+                for (int r = 0; r < kTileS; ++r) acc = fmaf(d2[r], s.H1[r][i], acc);
+                gW2[j * kLd + i] += acc;
+            }
+        }
+        {
+            const int i = j;  // this thread now owns input unit i of layer 2
+            float acc[kTileS];
+#pragma unroll
+            for (int r = 0; r < kTileS; ++r) acc[r] = 0.f;
+            for (int jj = 0; jj < kH; ++jj) {
+                const float wv = __bfloat162float(s.W2[jj * kH + i]);
+#pragma unroll
+                for (int r = 0; r < kTileS; ++r) acc[r] = fmaf(wv, s.G2[r][jj], acc[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < kTileS; ++r) {
+                const float da1 = acc[r] * s.G1[r][i];
+                gb1 += da1;
+#pragma unroll
+                for (int k = 0; k < kMaxIn; ++k) gW1[k] = fmaf(da1, s.X[r][k], gW1[k]);
+            }
+        }
+        __syncthreads();
+    }
+    // per-block partial gradients, packed as W1, b1, W2, b2, W3, b3
+    float *pp = partial + (size_t)blockIdx.x * n_params;
+#pragma unroll
+    for (int k = 0; k < kMaxIn; ++k)
+        if (k < nin) pp[(size_t)j * nin + k] = gW1[k];
+    float *pb1 = pp + (size_t)kH * nin, *pW2 = pb1 + kH, *pb2 = pW2 + (size_t)kH * kH, *pW3 = pb2 + kH,
+          *pb3 = pW3 + 2 * kH;
+    pb1[j] = gb1;
+    for (int i = 0; i < kH; ++i) pW2[(size_t)j * kH + i] = gW2[j * kLd + i];
+    pb2[j] = gb2;
+    pW3[j] = gW3_0;
+    pW3[kH + j] = gW3_1;
+    if (j == 0) {
+        pb3[0] = gb3_0;
+        pb3[1] = gb3_1;
+    }
+    // block loss sum (threads < 32 hold per-sample sums)
+    float l = lsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (j == 0) loss_partial[blockIdx.x] = l;
+}
+
+__global__ void mlp_reduce_kernel(const float *partial, int nb, long long n_params, float *grad,
+                                  const float *loss_partial, float *loss, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_params;
+         k += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b) s += partial[(size_t)b * n_params + k];
+        grad[k] = s;
+    }
+    if (loss && blockIdx.x == 0 && threadIdx.x == 0) {
+        float s = 0.f;
+        for (int b = 0; b < nb; ++b) s += loss_partial[b];
+        *loss = s / (float)n;
+    }
+}
+
+__global__ void mlp_adam_kernel(float *p, const float *g, float *m, float *v, long long n_params, float lr,
+                                float c1, float c2, __nv_bfloat16 *W1b, __nv_bfloat16 *W2b, __nv_bfloat16 *W3b,
+                                int nin)
+{
+    const long long nW1 = (long long)kH * nin, o2 = nW1 + kH, o3 = o2 + (long long)kH * kH + kH;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_params;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float gk = g[k];
+        const float mk = 0.9f * m[k] + 0.1f * gk;
+        const float vk = 0.999f * v[k] + 0.001f * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        const float pk = p[k] - lr * (mk / c1) / (sqrtf(vk / c2) + 1e-8f);
+        p[k] = pk;
+        if (k < nW1) W1b[k] = __float2bfloat16_rn(pk);
+        else if (k >= o2 && k < o2 + (long long)kH * kH) W2b[k - o2] = __float2bfloat16_rn(pk);
+        else if (k >= o3 && k < o3 + 2 * kH) W3b[k - o3] = __float2bfloat16_rn(pk);
+    }
+}
+
+__global__ void __launch_bounds__(kH) mlp_infer_kernel(MlpW w, const float *feat, const float *tau_fcc, long long n,
+                                                       float threshold, float *tau_out, float *conf_out, float *raw_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
+    load_weights(s, w);
+    __syncthreads();
+    const long long n_tiles = (n + kTileS - 1) / kTileS;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const long long base = t * kTileS;
+        const int ns = (int)min((long long)kTileS, n - base);
+        load_x(s, feat, base, ns, w.nin);
+        forward_tile(s, w.nin, false);
+        if (threadIdx.x < ns) {
+            const int r = threadIdx.x;
+            const float y0 = s.Y[r][0], c = 1.f / (1.f + expf(-s.Y[r][1]));
+            tau_out[base + r] = (c >= threshold || !tau_fcc) ? y0 : tau_fcc[base + r];
+            if (conf_out) conf_out[base + r] = c;
+            if (raw_out) raw_out[base + r] = y0;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void bf16_copy_kernel(const float *src, __nv_bfloat16 *dst, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        dst[k] = __float2bfloat16_rn(src[k]);
+}
+
+}  // namespace
+}  // namespace fcc
+
+struct fcc_mlp {
+    int device = 0, nin = 0, num_sms = 0;
+    long long n_params = 0;
+    float lambda = 0.1f;
+    float *scale = nullptr;  // [nin]
+    long long step = 0;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    __nv_bfloat16 *Wb = nullptr;  // W1, W2, W3 BF16 copies, contiguous
+    float *partial = nullptr, *loss_partial = nullptr;
+    int nb = 0;
+};
+
+using namespace fcc;
+
+namespace {
+
+MlpW weights(const fcc_mlp *h)
+{
+    MlpW w;
+    w.W1 = h->Wb;
+    w.W2 = h->Wb + (size_t)kH * h->nin;
+    w.W3 = w.W2 + (size_t)kH * kH;
+    w.b1 = h->p + (size_t)kH * h->nin;
+    w.b2 = w.b1 + kH + (size_t)kH * kH;
+    w.b3 = w.b2 + kH + 2 * kH;
+    w.nin = h->nin;
+    w.scale = h->scale;
+    return w;
+}
+
+fcc_status_t refresh_bf16(fcc_mlp *h, cudaStream_t st)
+{
+    const long long nW1 = (long long)kH * h->nin;
+    bf16_copy_kernel<<<64, 256, 0, st>>>(h->p, h->Wb, nW1);
+    bf16_copy_kernel<<<64, 256, 0, st>>>(h->p + nW1 + kH, h->Wb + nW1, (long long)kH * kH);
+    bf16_copy_kernel<<<8, 256, 0, st>>>(h->p + nW1 + kH + (long long)kH * kH + kH, h->Wb + nW1 + (long long)kH * kH,
+                                        2 * kH);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "bf16 weight copy");
+}
+
+size_t grad_smem() { return sizeof(MlpSmem) + sizeof(float) * kH * kLd; }
+
+fcc_status_t run_grad(fcc_mlp *h, const float *feat, const float *tt, const float *tf, long long n, float *loss,
+                      cudaStream_t st)
+{
+    static bool attr[64] = {};
+    if (!attr[h->device & 63]) {
+        FCC_CUDA_TRY(cudaFuncSetAttribute(mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()));
+        attr[h->device & 63] = true;
+    }
+    const long long tiles = (n + kTileS - 1) / kTileS;
+    const int grid = (int)std::min<long long>(tiles, h->nb);
+    mlp_grad_kernel<<<grid, kH, grad_smem(), st>>>(weights(h), feat, tt, tf, n, h->lambda, h->partial, h->n_params,
+                                                   h->loss_partial);
+    mlp_reduce_kernel<<<(int)((h->n_params + 255) / 256), 256, 0, st>>>(h->partial, grid, h->n_params, h->g,
+                                                                        h->loss_partial, loss, n);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp gradient kernels");
+}
+
+}  // namespace
+
+extern "C" {
+
+long long fcc_mlp_num_params(int n_in, int hidden)
+{
+    return (long long)hidden * n_in + hidden + (long long)hidden * hidden + hidden + 2LL * hidden + 2;
+}
+
+fcc_status_t fcc_mlp_create(int n_in, int hidden, const float *h_in_scale, double conf_weight, const float *h_params,
+                            int device, fcc_mlp_t **out)
+{
+    if (!out || !h_params) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (hidden != kH) return fail(FCC_ERR_UNSUPPORTED, "hidden width must be 128");
+    if (n_in < 1 || n_in > kMaxIn) return fail(FCC_ERR_UNSUPPORTED, "n_in must be in [1, 32]");
+    if (!(conf_weight >= 0)) return fail(FCC_ERR_INVALID_ARG, "conf_weight < 0");
+    int dev = device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(FCC_ERR_CUDA, "no CUDA device");
+    DeviceScope scope(dev);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    fcc_mlp *h = new (std::nothrow) fcc_mlp();
+    if (!h) return fail(FCC_ERR_OOM, "host allocation");
+    h->device = dev;
+    h->nin = n_in;
+    h->lambda = (float)conf_weight;
+    h->n_params = fcc_mlp_num_params(n_in, hidden);
+    cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    h->nb = std::max(1, h->num_sms);
+    const size_t np_ = (size_t)h->n_params;
+    const size_t nwb = (size_t)kH * n_in + (size_t)kH * kH + 2 * kH;
+    if (e == cudaSuccess) e = cudaMalloc(&h->p, np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->m, np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->v, np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->g, np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->Wb, nwb * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&h->partial, (size_t)h->nb * np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->loss_partial, (size_t)h->nb * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->scale, (size_t)n_in * sizeof(float));
+    if (e == cudaSuccess) {
+        std::vector<float> sc(n_in, 1.f);
+        if (h_in_scale) sc.assign(h_in_scale, h_in_scale + n_in);
+        e = cudaMemcpy(h->scale, sc.data(), (size_t)n_in * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h->p, h_params, np_ * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->m, 0, np_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->v, 0, np_ * sizeof(float));
+    fcc_status_t st = e == cudaSuccess ? refresh_bf16(h, 0) : cuda_fail(e, "mlp allocation");
+    if (st == FCC_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "mlp init");
+    }
+    if (st != FCC_OK) {
+        fcc_mlp_destroy(h);
+        return st;
+    }
+    *out = h;
+    return FCC_OK;
+}
+
+void fcc_mlp_destroy(fcc_mlp_t *h)
+{
+    if (!h) return;
+    DeviceScope scope(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->p);
+    cudaFree(h->m);
+    cudaFree(h->v);
+    cudaFree(h->g);
+    cudaFree(h->Wb);
+    cudaFree(h->partial);
+    cudaFree(h->loss_partial);
+    cudaFree(h->scale);
+    delete h;
+}
+
+fcc_status_t fcc_mlp_get_state(const fcc_mlp_t *h, float *params, float *m, float *v, long long *step)
+{
+    if (!h) return fail(FCC_ERR_INVALID_ARG, "null mlp");
+    DeviceScope scope(h->device);
+    const size_t b = (size_t)h->n_params * sizeof(float);
+    FCC_CUDA_TRY(cudaDeviceSynchronize());
+    if (params) FCC_CUDA_TRY(cudaMemcpy(params, h->p, b, cudaMemcpyDeviceToHost));
+    if (m) FCC_CUDA_TRY(cudaMemcpy(m, h->m, b, cudaMemcpyDeviceToHost));
+    if (v) FCC_CUDA_TRY(cudaMemcpy(v, h->v, b, cudaMemcpyDeviceToHost));
+    if (step) *step = h->step;
+    return FCC_OK;
+}
+
+fcc_status_t fcc_mlp_set_state(fcc_mlp_t *h, const float *params, const float *m, const float *v, long long step)
+{
+    if (!h || !params) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    if (step < 0) return fail(FCC_ERR_INVALID_ARG, "step < 0");
+    DeviceScope scope(h->device);
+    const size_t b = (size_t)h->n_params * sizeof(float);
+    FCC_CUDA_TRY(cudaDeviceSynchronize());
+    FCC_CUDA_TRY(cudaMemcpy(h->p, params, b, cudaMemcpyHostToDevice));
+    if (m) FCC_CUDA_TRY(cudaMemcpy(h->m, m, b, cudaMemcpyHostToDevice));
+    else FCC_CUDA_TRY(cudaMemset(h->m, 0, b));
+    if (v) FCC_CUDA_TRY(cudaMemcpy(h->v, v, b, cudaMemcpyHostToDevice));
+    else FCC_CUDA_TRY(cudaMemset(h->v, 0, b));
+    h->step = step;
+    fcc_status_t st = refresh_bf16(h, 0);
+    if (st != FCC_OK) return st;
+    FCC_CUDA_TRY(cudaDeviceSynchronize());
+    return FCC_OK;
+}
+
+fcc_status_t fcc_mlp_gradient(fcc_mlp_t *h, const float *d_feat, const float *d_tau_true, const float *d_tau_fcc,
+                              long long n, float *d_grad, float *d_loss, void *stream)
+{
+    if (!h || !d_feat || !d_tau_true || !d_tau_fcc || !d_grad) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    if (n <= 0) return fail(FCC_ERR_INVALID_ARG, "n <= 0");
+    DeviceScope scope(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fcc_status_t s = run_grad(h, d_feat, d_tau_true, d_tau_fcc, n, d_loss, st);
+    if (s != FCC_OK) return s;
+    FCC_CUDA_TRY(cudaMemcpyAsync(d_grad, h->g, (size_t)h->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return FCC_OK;
+}
+
+fcc_status_t fcc_mlp_train_step(fcc_mlp_t *h, const float *d_feat, const float *d_tau_true, const float *d_tau_fcc,
+                                long long n, float lr, float *d_loss, void *stream)
+{
+    if (!h || !d_feat || !d_tau_true || !d_tau_fcc) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    if (n <= 0 || !(lr > 0)) return fail(FCC_ERR_INVALID_ARG, "n <= 0 or lr <= 0");
+    DeviceScope scope(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    fcc_status_t s = run_grad(h, d_feat, d_tau_true, d_tau_fcc, n, d_loss, st);
+    if (s != FCC_OK) return s;
+    h->step += 1;
+    const float c1 = 1.f - powf(0.9f, (float)h->step), c2 = 1.f - powf(0.999f, (float)h->step);
+    const long long nW1 = (long long)kH * h->nin;
+    mlp_adam_kernel<<<(int)((h->n_params + 255) / 256), 256, 0, st>>>(
+        h->p, h->g, h->m, h->v, h->n_params, lr, c1, c2, h->Wb, h->Wb + nW1, h->Wb + nW1 + (long long)kH * kH, h->nin);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp adam");
+}
+
+fcc_status_t fcc_mlp_infer(fcc_mlp_t *h, const float *d_feat, const float *d_tau_fcc, long long n, float threshold,
+                           float *d_tau, float *d_conf, float *d_raw, void *stream)
+{
+    if (!h) return fail(FCC_ERR_INVALID_ARG, "null mlp");
+    if (n < 0) return fail(FCC_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return FCC_OK;
+    if (!d_feat || !d_tau) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    DeviceScope scope(h->device);
+    static bool attr[64] = {};
+    if (!attr[h->device & 63]) {
+        FCC_CUDA_TRY(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(MlpSmem)));
+        attr[h->device & 63] = true;
+    }
+    const long long tiles = (n + kTileS - 1) / kTileS;
+    const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * 2);
+    mlp_infer_kernel<<<grid, kH, sizeof(MlpSmem), static_cast<cudaStream_t>(stream)>>>(
+        weights(h), d_feat, d_tau_fcc, n, threshold, d_tau, d_conf, d_raw);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp inference");
+}
+
+}  // extern "C"

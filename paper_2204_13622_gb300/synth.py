@@ -200,3 +200,71 @@ def stft_domain_spectra(T: int, xyz: np.ndarray, fs: float, N: int, hop: int, se
         out[t0:t1] = X
         del src, ramp, X, noise, ph
     return out
+
+
+# ----------------------------------------------------------------------------
+# learned head: two-microphone pair spectra with a known TDoA, initial weights
+# ----------------------------------------------------------------------------
+def pair_delay_spectra(n: int, N: int, tau_max: float, seed: int, device="cpu",
+                       snr_db: tuple = (-5.0, 30.0), start: int = 0):
+    """Two-microphone spectra [n, 2, N/2+1] complex64 with a known TDoA each.
+
+    Pair-frame s draws a true TDoA t_s uniform in [-tau_max, tau_max] (samples,
+    tau = t_0 - t_1 as for pair (0, 1)), an SNR uniform in `snr_db`, and a
+    source that is white or pink (1/f power) with equal odds, complex Gaussian
+    per bin with unit mean power.  Microphone 0 hears S(f); microphone 1 hears
+    S(f) exp(+j 2 pi f t_s / N), i.e. mic 1 lags mic 0 by -t_s samples, so the
+    pair's correlation peaks at tau = t_s.  Each microphone adds independent
+    complex white noise of power 10^(-SNR/10).  Returns (X, t [n] float64
+    numpy, snr [n] float64 numpy).  Sample s depends only on (seed, start + s)
+    blocks of 2^16, so chunked generation gives the same set.
+    """
+    import torch
+
+    B = N // 2 + 1
+    dev = torch.device(device)
+    X = torch.empty((n, 2, B), dtype=torch.complex64, device=dev)
+    t_all = np.empty(n)
+    snr_all = np.empty(n)
+    f = torch.arange(B, device=dev, dtype=torch.float64)
+    pink = 1.0 / torch.sqrt(torch.clamp(f, min=1.0))
+    pink = (pink / torch.sqrt((pink ** 2).mean())).to(torch.float32)
+    blk = 1 << 16
+    s = 0
+    while s < n:
+        g0 = (start + s) // blk
+        off = (start + s) - g0 * blk
+        m = min(n - s, blk - off)
+        rng = np.random.default_rng([int(seed), int(g0)])
+        t = rng.uniform(-tau_max, tau_max, size=blk)[off:off + m]
+        snr = rng.uniform(snr_db[0], snr_db[1], size=blk)[off:off + m]
+        is_pink = rng.integers(0, 2, size=blk)[off:off + m].astype(bool)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(int(seed) * 1000003 + int(g0))
+        src = torch.randn((blk, B), dtype=torch.complex64, device=dev, generator=gen)[off:off + m]
+        noise = torch.randn((blk, 2, B), dtype=torch.complex64, device=dev, generator=gen)[off:off + m]
+        shape = torch.where(torch.tensor(is_pink, device=dev)[:, None], pink[None, :],
+                            torch.ones_like(pink)[None, :])
+        src = src * shape
+        ph = (2.0 * math.pi / N) * torch.tensor(t, dtype=torch.float64, device=dev)[:, None] * f
+        ramp = torch.polar(torch.ones_like(ph, dtype=torch.float32), ph.to(torch.float32))
+        amp = torch.tensor(10.0 ** (-snr / 20.0), dtype=torch.float32, device=dev)[:, None]
+        X[s:s + m, 0] = src + noise[:, 0] * amp
+        X[s:s + m, 1] = src * ramp + noise[:, 1] * amp
+        t_all[s:s + m] = t
+        snr_all[s:s + m] = snr
+        s += m
+    return X, t_all, snr_all
+
+
+def mlp_init_params(n_in: int, hidden: int, seed: int) -> np.ndarray:
+    """Initial parameters of the learned head, packed W1[H][n_in], b1[H],
+    W2[H][H], b2[H], W3[2][H], b3[2]: weights uniform in +-1/sqrt(fan_in),
+    biases zero.  float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((hidden, n_in), (hidden, hidden), (2, hidden)):
+        a = 1.0 / math.sqrt(fan_in)
+        parts.append(rng.uniform(-a, a, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library loads and
-exports every function include/fcc.h declares, and the binding agrees."""
+exports every function include/*.h declares, and the binding agrees."""
 import ctypes
 import os
 import re
@@ -18,9 +18,13 @@ def lib():
 
 
 def declared_functions():
-    txt = open(os.path.join(ROOT, "include", "fcc.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(fcc_[a-z_]+)\s*\(", txt)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(fcc_[a-z_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_header_lists_every_binding_export():
