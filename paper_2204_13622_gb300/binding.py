@@ -26,7 +26,12 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc",
            # include/fcc_mlp.h
            "fcc_mlp_num_params", "fcc_mlp_create", "fcc_mlp_destroy", "fcc_mlp_get_state",
-           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer"]
+           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer",
+           # include/fcc_tune.h
+           "fcc_plan_geometry", "fcc_plan_autotune",
+           # include/fcc_batch.h
+           "fcc_batch_create", "fcc_batch_destroy", "fcc_batch_info", "fcc_batch_array_info", "fcc_batch_bind",
+           "fcc_batch_run", "fcc_batch_sync"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -42,6 +47,21 @@ class PlanInfo(ctypes.Structure):
                 ("center", ctypes.c_int), ("K", ctypes.c_int), ("K_even", ctypes.c_int),
                 ("K_odd", ctypes.c_int), ("prec", ctypes.c_int), ("delta", ctypes.c_double),
                 ("fs", ctypes.c_double), ("c", ctypes.c_double)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int), ("warps_per_group", ctypes.c_int), ("groups", ctypes.c_int),
+                ("frames_per_stage", ctypes.c_int), ("stages", ctypes.c_int), ("threads", ctypes.c_int),
+                ("smem_bytes", ctypes.c_longlong)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_arrays", ctypes.c_int), ("n_classes", ctypes.c_int), ("n_jobs", ctypes.c_int),
+                ("n_bases", ctypes.c_int), ("frames", ctypes.c_longlong), ("pair_frames", ctypes.c_longlong),
+                ("spectra_bytes", ctypes.c_double), ("result_bytes", ctypes.c_double)]
+
+
+FCC_BATCH_AUTOTUNE = 1
 
 
 class FccError(RuntimeError):
@@ -92,6 +112,21 @@ def lib():
         L.fcc_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
         L.fcc_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp]
         L.fcc_mlp_infer.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp, _vp, _vp]
+        L.fcc_plan_geometry.argtypes = [_vp, ctypes.POINTER(Geometry)]
+        L.fcc_plan_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, _dp]
+        L.fcc_batch_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(_vp)]
+        L.fcc_batch_destroy.argtypes = [_vp]
+        L.fcc_batch_destroy.restype = None
+        L.fcc_batch_info.argtypes = [_vp, ctypes.POINTER(BatchInfo)]
+        L.fcc_batch_array_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(PlanInfo)]
+        L.fcc_batch_bind.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                     ctypes.POINTER(_vp)]
+        L.fcc_batch_run.argtypes = [_vp, _vp]
+        L.fcc_batch_sync.argtypes = [_vp, _vp]
+        for name in ("fcc_plan_geometry", "fcc_plan_autotune", "fcc_batch_create", "fcc_batch_info",
+                     "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_mlp_create", "fcc_mlp_get_state", "fcc_mlp_set_state", "fcc_mlp_gradient",
                      "fcc_mlp_train_step", "fcc_mlp_infer"):
             getattr(L, name).restype = ctypes.c_int
@@ -245,6 +280,19 @@ class Plan:
         """Synchronise and raise if a kernel latched an error (NaN/Inf input, timeout)."""
         check(lib().fcc_plan_sync(self._h, _stream(stream, self.device)), "fcc_plan_sync")
 
+    def geometry(self) -> dict:
+        g = Geometry()
+        check(lib().fcc_plan_geometry(self._h, ctypes.byref(g)), "fcc_plan_geometry")
+        return {k: getattr(g, k) for k, _ in Geometry._fields_}
+
+    def autotune(self, cache_path: str | None = None, force: bool = False, max_candidates: int = 0) -> float:
+        """Time the FP32 kernel's candidate tile shapes and keep the fastest
+        (fcc_plan_autotune); returns microseconds per frame."""
+        us = ctypes.c_double()
+        check(lib().fcc_plan_autotune(self._h, cache_path.encode() if cache_path else None, int(force),
+                                      int(max_candidates), ctypes.byref(us)), "fcc_plan_autotune")
+        return us.value
+
 
 def plan_bases_noalloc(n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0, mic_xyz=None,
                        c: float = 343.0, K: int = 0, energy: float = 0.999, device: int = 0, stream=None):
@@ -356,3 +404,108 @@ class MLP:
                                   _ptr(out.get("conf")), _ptr(out.get("raw")), _stream(stream, feat.device)),
               "fcc_mlp_infer")
         return out
+
+
+def _desc(n_mics, fs, N, lag_den, tau_max=0.0, mic_xyz=None, c=343.0, K=0, energy=0.999, keep=None):
+    xyz = None
+    if mic_xyz is not None:
+        xyz = np.ascontiguousarray(mic_xyz, np.float64).reshape(n_mics, 3)
+        if keep is not None:
+            keep.append(xyz)
+    return PlanDesc(int(n_mics), xyz.ctypes.data_as(_dp) if xyz is not None else None, float(fs), int(N), float(c),
+                    float(tau_max), int(lag_den), int(K), float(energy), 0, 0)
+
+
+_DESC_KEYS = ("n_mics", "fs", "N", "lag_den", "tau_max", "mic_xyz", "c", "K", "energy")
+
+
+class Batch:
+    """Many arrays in persistent launches under one CUDA graph (include/fcc_batch.h).
+
+    `arrays`: list of dicts with the Plan keywords (n_mics, fs, N, lag_den and
+    optionally tau_max, mic_xyz, c, K, energy) plus T (frames); other keys are
+    ignored."""
+
+    def __init__(self, arrays, device: int | None = None, autotune: bool = False, tune_cache: str | None = None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        keep = []
+        n = len(arrays)
+        descs = (PlanDesc * n)()
+        T = (ctypes.c_longlong * n)()
+        for a, d in enumerate(arrays):
+            kw = {k: v for k, v in d.items() if k in _DESC_KEYS}
+            descs[a] = _desc(keep=keep, **kw)
+            T[a] = int(d["T"])
+        h = _vp()
+        check(lib().fcc_batch_create(descs, T, n, self.device, FCC_BATCH_AUTOTUNE if autotune else 0,
+                                     tune_cache.encode() if tune_cache else None, ctypes.byref(h)),
+              "fcc_batch_create")
+        self._h = h
+        self.T = [int(d["T"]) for d in arrays]
+        self.arrays = []
+        for a in range(n):
+            info = PlanInfo()
+            check(lib().fcc_batch_array_info(h, a, ctypes.byref(info)), "fcc_batch_array_info")
+            self.arrays.append({k: getattr(info, k) for k, _ in PlanInfo._fields_})
+        self._bound = None
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        check(lib().fcc_batch_info(self._h, ctypes.byref(i)), "fcc_batch_info")
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def outputs(self, tau_hat: bool = True):
+        """Device output tensors for every array: list of dicts."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        out = []
+        for a, info in enumerate(self.arrays):
+            o = {"lag_idx": torch.empty((self.T[a], info["P"]), dtype=torch.int32, device=dev),
+                 "peak": torch.empty((self.T[a], info["P"]), dtype=torch.float32, device=dev)}
+            if tau_hat:
+                o["tau_hat"] = torch.empty((self.T[a], info["P"]), dtype=torch.float32, device=dev)
+            out.append(o)
+        return out
+
+    def bind(self, spectra, outputs):
+        """Bind device spectra (list of complex64 [T, M, B] tensors) and outputs."""
+        n = len(self.arrays)
+        if len(spectra) != n or len(outputs) != n:
+            raise ValueError("one spectra tensor and one output dict per array")
+        for a, X in enumerate(spectra):
+            info = self.arrays[a]
+            if tuple(X.shape) != (self.T[a], info["M"], info["B"]) or not X.is_contiguous():
+                raise ValueError(f"array {a}: spectra must be contiguous [{self.T[a]}, {info['M']}, {info['B']}]")
+        P = (_vp * n)
+        sp, ix, pk = P(), P(), P()
+        has_tau = any("tau_hat" in o for o in outputs)
+        tu = P() if has_tau else None
+        for a in range(n):
+            sp[a] = spectra[a].data_ptr()
+            ix[a] = outputs[a]["lag_idx"].data_ptr()
+            pk[a] = outputs[a]["peak"].data_ptr()
+            if has_tau:
+                tu[a] = outputs[a]["tau_hat"].data_ptr() if "tau_hat" in outputs[a] else None
+        check(lib().fcc_batch_bind(self._h, sp, ix, pk, tu), "fcc_batch_bind")
+        self._bound = (spectra, outputs)  # keep the tensors alive while bound
+
+    def run(self, stream=None):
+        check(lib().fcc_batch_run(self._h, _stream(stream, self.device)), "fcc_batch_run")
+
+    def sync(self, stream=None):
+        check(lib().fcc_batch_sync(self._h, _stream(stream, self.device)), "fcc_batch_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fcc_batch_destroy(self._h)
+            self._h = None
+            self._bound = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -109,6 +109,34 @@ void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<fl
     }
 }
 
+}  // namespace
+
+fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g)
+{
+    plan->geo = g;
+    std::vector<float> basis, recon;
+    if (g.C) pack_tables(plan, basis, recon);
+    else basis.assign(4, 0.f), recon.assign(4, 0.f);  // N > 1024: no FP32 kernel
+    float *nb = nullptr, *nr = nullptr;
+    cudaError_t e = cudaMalloc(&nb, basis.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&nr, recon.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(nb, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(nr, recon.data(), recon.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(nb);
+        cudaFree(nr);
+        return cuda_fail(e, "plan tables");
+    }
+    if (plan->d_basis || plan->d_recon) cudaDeviceSynchronize();  // no launch may still read the old tables
+    cudaFree(plan->d_basis);
+    cudaFree(plan->d_recon);
+    plan->d_basis = nb;
+    plan->d_recon = nr;
+    return FCC_OK;
+}
+
+namespace {
+
 void free_plan(fcc_plan *p)
 {
     if (!p) return;
@@ -243,17 +271,11 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
     p->n_slots = (int)slots.size();
     if (p->kh) {
         st = choose_fp32_geometry(p);
+        if (st == FCC_OK) st = set_fp32_geometry(p, p->geo);
         if (st != FCC_OK) {
             free_plan(p);
             return st;
         }
-        std::vector<float> basis, recon;
-        if (p->geo.C) pack_tables(p, basis, recon);
-        else basis.assign(4, 0.f), recon.assign(4, 0.f);  // N > 1024: no FP32 kernel
-        e = cudaMalloc(&p->d_basis, basis.size() * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_recon, recon.size() * sizeof(float));
-        if (e == cudaSuccess) e = cudaMemcpy(p->d_basis, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(p->d_recon, recon.data(), recon.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->d_slots, slots.size() * sizeof(Slot));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_slots, slots.data(), slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);

@@ -84,11 +84,16 @@ __device__ __forceinline__ int rec_off(int R, int B) { return R * B * 8 + ((R & 
 __device__ __forceinline__ int lone_off(int R, int B, int Q) { return R * B * 8 + ((R & 1) ? 0 : 16 * Q); }
 
 
+// The whole per-tile pipeline for one plan: this CTA processes tiles
+// tile_base + k * tile_stride, k = 0 .. n_local - 1, with the geometry and tables
+// of `p` laid out from `smem`.  Warps beyond the plan's G * GW only help load the
+// tables.  Every barrier this call initialises is idle again when it returns
+// (all copies it issued have landed).
 // RS = fold records per lane per row = max(1, N / 128) (N/4 records over 32 lanes).
 template <int KH, int RS>
-__global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel(const Fp32Params p)
+__device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *smem, long long tile_base,
+                                           long long tile_stride, int n_local)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
     const int frame_bytes = p.frame_floats * 4;
     const SmemLayout lay = smem_layout(p.S, p.n_slots, p.Q, KH, p.C, p.BS, p.center, p.F, frame_bytes);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bar_off);
@@ -101,10 +106,8 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp / p.GW, wig = warp - group * p.GW;
-    const int n_local = (p.n_tiles > (int)blockIdx.x)
-                            ? (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
-                            : 0;
-    const bool leader = (wig == 0 && lane == 0);
+    const bool member = group < p.G;  // this warp belongs to one of the plan's groups
+    const bool leader = member && wig == 0 && lane == 0;
 
     // ---- prologue: barriers, tables into shared memory
     if (threadIdx.x == 0) {
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
     __syncthreads();
 
     auto tile_src = [&](int k, int &nf) {
-        const long long tile = (long long)blockIdx.x + (long long)k * gridDim.x;
+        const long long tile = tile_base + (long long)k * tile_stride;
         const long long f0 = tile * p.F;
         nf = (int)min((long long)p.F, p.T - f0);
         return f0;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
     const unsigned FULLM = 0xffffffffu;
     int k_done = group - p.G;  // last tile fully consumed by this group
 
-    for (int k = group; k < n_local; k += p.G) {
+    for (int k = group; member && k < n_local; k += p.G) {
         const int s = k % p.S;
         const unsigned par = (unsigned)(k / p.S) & 1u;
         int nf;
@@ -478,6 +481,49 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
 }
 
 template <int KH, int RS>
+__global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel(const __grid_constant__ Fp32Params p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int n_local = (p.n_tiles > (int)blockIdx.x)
+                            ? (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                            : 0;
+    fp32_tiles<KH, RS>(p, smem, blockIdx.x, gridDim.x, n_local);
+}
+
+// Batched form: many plans of one (KH, RS) class in one persistent launch.  A
+// CTA takes jobs (one plan, a run of its tiles) from a shared counter in the
+// host's order (largest first); per job it copies the plan's parameters into a
+// shared-memory header, runs the same tile pipeline, then invalidates the
+// job's barriers so the next job can lay out its own ring.
+template <int KH, int RS>
+__global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_batch_kernel(const __grid_constant__ BatchParams bp)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Fp32Params *hdr = reinterpret_cast<Fp32Params *>(smem);
+    int *s_job = reinterpret_cast<int *>(smem + kBatchHeaderBytes - 8);
+    unsigned char *body = smem + kBatchHeaderBytes;
+    for (;;) {
+        if (threadIdx.x == 0) *s_job = atomicAdd(bp.counter, 1);
+        __syncthreads();
+        const int j = *s_job;
+        if (j >= bp.n_jobs) break;
+        const BatchJob job = bp.jobs[j];
+        {
+            const int *src = reinterpret_cast<const int *>(bp.arrays + job.array);
+            int *dst = reinterpret_cast<int *>(hdr);
+            for (int e = threadIdx.x; e < (int)(sizeof(Fp32Params) / sizeof(int)); e += blockDim.x) dst[e] = src[e];
+        }
+        __syncthreads();
+        fp32_tiles<KH, RS>(*hdr, body, job.tile0, 1, job.n_tiles);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t *bars = reinterpret_cast<uint64_t *>(body);
+            for (int s = 0; s < 3 * hdr->S; ++s) mbar_inval(&bars[s]);
+        }
+    }
+}
+
+template <int KH, int RS>
 fcc_status_t launch_inst(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
 {
     static bool attr_set[64] = {};
@@ -509,29 +555,27 @@ fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t
 
 }  // namespace
 
-// Choose chunks per slot (C), warps per group (GW), groups (G), frames per
-// stage (F) and the ring depth (S = G * stages per group) for this plan.  Each
-// stage is only ever filled for, and released by, one group, so every group
-// sees a plain single-consumer ring and a phase parity can never be stale.
-// FCC_FP32_GROUPS / FCC_FP32_STAGES_PER_GROUP pin G and S/G (tuning only).
-fcc_status_t choose_fp32_geometry(fcc_plan *plan)
+// Every geometry that fits: chunks per slot (C), warps per group (GW), groups
+// (G), frames per stage (F) and the ring depth (S = G * stages per group), best
+// heuristic score first.  Each stage is only ever filled for, and released by,
+// one group, so every group sees a plain single-consumer ring and a phase parity
+// can never be stale.  The shared-memory budget leaves room for the batched
+// kernel's header, so one geometry serves both launch forms.
+fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out)
 {
+    out.clear();
     const fcc_plan_info_t &in = plan->info;
     const int kh = plan->kh;
     const int n_slots = plan->n_slots;
     const int frame_bytes = in.M * in.B * 8;
-    if (in.Q > 32 * kMaxRowSlots) return FCC_OK;  // N > 1024: the FP32 kernel is not used
+    if (in.Q > 32 * kMaxRowSlots || kh == 0) return FCC_OK;  // N > 1024: the FP32 kernel is not used
     int smem_max = 0;
     FCC_CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, plan->device));
-    smem_max = std::min(smem_max, 232448);
-    const char *eg = getenv("FCC_FP32_GROUPS");
-    const char *es = getenv("FCC_FP32_STAGES_PER_GROUP");
-    const int want_g = eg ? atoi(eg) : 0, want_sg = es ? atoi(es) : 0;
+    smem_max = std::min(smem_max, 232448) - kBatchHeaderBytes;
     // basis row: KH even then KH odd weights, padded to an odd number of 16-byte units
     const int BS = ((2 * kh / 4) % 2 == 0) ? 2 * kh + 4 : 2 * kh;
     const int maxw = max_compute_warps(kh);
-    Fp32Geometry best{};
-    double best_score = -1.0;
+    std::vector<std::pair<double, Fp32Geometry>> scored;
     for (int C = 4; C <= 16 && C <= in.Q; C <<= 1) {
         const int SB = 32 / C;
         const int nb = (n_slots + SB - 1) / SB;
@@ -539,9 +583,7 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan)
         for (int F = 1; nb * F <= maxw; ++F) {
             const int GW = nb * F;
             for (int G = maxw / GW; G >= 1; --G) {
-                if (want_g && G != want_g) continue;
                 for (int Sg = 2; Sg >= 1; --Sg) {
-                    if (want_sg && Sg != want_sg) continue;
                     const int S = G * Sg;
                     const SmemLayout L = smem_layout(S, n_slots, in.Q, kh, C, BS, in.center, F, frame_bytes);
                     if (L.total > (size_t)smem_max) continue;
@@ -550,26 +592,44 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan)
                     // stages by 1.4x); fewer chunks mean a shorter shuffle
                     // reduction; a second stage per group only breaks ties
                     const double score = util * (G * GW) * (1.0 - 0.1 * (C / 4 - 1)) + (Sg >= 2 ? 0.01 : 0.0);
-                    if (score > best_score) {
-                        best_score = score;
-                        best = Fp32Geometry{C, SB, nb * 32, GW, G, F, S, BS, L.total};
-                    }
-                    break;  // the deepest ring that fits for this G
+                    scored.push_back({score, Fp32Geometry{C, SB, nb * 32, GW, G, F, S, BS, L.total}});
                 }
             }
         }
     }
-    if (best_score < 0) return fail(FCC_ERR_UNSUPPORTED, "frame too large for the shared-memory ring");
-    plan->geo = best;
+    std::stable_sort(scored.begin(), scored.end(),
+                     [](const auto &a, const auto &b) { return a.first > b.first; });
+    for (auto &e : scored) out.push_back(e.second);
     return FCC_OK;
 }
 
-fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
-                         float *tau, float *coef, float *corr, cudaStream_t st)
+// The heuristic choice (first candidate); FCC_FP32_GROUPS /
+// FCC_FP32_STAGES_PER_GROUP pin G and S/G (tuning only).
+fcc_status_t choose_fp32_geometry(fcc_plan *plan)
+{
+    std::vector<Fp32Geometry> cand;
+    fcc_status_t st = fp32_candidates(plan, cand);
+    if (st != FCC_OK) return st;
+    const fcc_plan_info_t &in = plan->info;
+    if (in.Q > 32 * kMaxRowSlots || plan->kh == 0) return FCC_OK;
+    const char *eg = getenv("FCC_FP32_GROUPS");
+    const char *es = getenv("FCC_FP32_STAGES_PER_GROUP");
+    const int want_g = eg ? atoi(eg) : 0, want_sg = es ? atoi(es) : 0;
+    for (const Fp32Geometry &g : cand) {
+        if (want_g && g.G != want_g) continue;
+        if (want_sg && g.S / g.G != want_sg) continue;
+        plan->geo = g;
+        return FCC_OK;
+    }
+    return fail(FCC_ERR_UNSUPPORTED, "frame too large for the shared-memory ring");
+}
+
+// Kernel parameters of one call of the plan (geometry and tables from the plan).
+Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                            float *tau, float *coef, float *corr, unsigned *err)
 {
     const fcc_plan_info_t &in = plan->info;
     const Fp32Geometry &g = plan->geo;
-    if (g.G == 0) return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
     Fp32Params prm{};
     prm.spectra = spectra;
     prm.T = T;
@@ -587,9 +647,7 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     prm.G = g.G;
     prm.F = g.F;
     prm.S = g.S;
-    const long long n_tiles = (T + g.F - 1) / g.F;
-    if (n_tiles > 0x7fffffffLL) return fail(FCC_ERR_UNSUPPORTED, "too many frames for one call");
-    prm.n_tiles = (int)n_tiles;
+    prm.n_tiles = (int)std::min<long long>((T + g.F - 1) / g.F, 0x7fffffffLL);
     prm.frame_floats = in.M * in.B * 2;
     const size_t frame_bytes = (size_t)in.M * in.B * 8;
     prm.bulk = (frame_bytes % 16 == 0) && ((reinterpret_cast<uintptr_t>(spectra) & 15) == 0);
@@ -606,7 +664,18 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     prm.out_tau = tau;
     prm.out_coef = coef;
     prm.out_corr = corr;
-    prm.err = plan->d_err;
+    prm.err = err;
+    return prm;
+}
+
+fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                         float *tau, float *coef, float *corr, cudaStream_t st)
+{
+    const Fp32Geometry &g = plan->geo;
+    if (g.G == 0) return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
+    const long long n_tiles = (T + g.F - 1) / g.F;
+    if (n_tiles > 0x7fffffffLL) return fail(FCC_ERR_UNSUPPORTED, "too many frames for one call");
+    const Fp32Params prm = make_fp32_params(plan, spectra, T, idx, peak, tau, coef, corr, plan->d_err);
     const int grid = (int)std::min<long long>(n_tiles, (long long)plan->num_sms);
     switch (plan->kh) {
     case 2: return launch_kh<2>(plan, prm, st, grid);
@@ -616,5 +685,50 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     default: return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
     }
 }
+
+int fp32_threads(int kh) { return max_compute_warps(kh) * 32; }
+
+namespace {
+template <int KH, int RS>
+fcc_status_t launch_batch_inst(const BatchParams &bp, int grid, size_t smem, cudaStream_t st)
+{
+    if (grid == 0) {  // prepare only: raise the shared-memory limit (not capturable)
+        cudaError_t e = cudaFuncSetAttribute(fcc_fp32_batch_kernel<KH, RS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+        return e == cudaSuccess ? FCC_OK : cuda_fail(e, "cudaFuncSetAttribute(fcc_fp32_batch_kernel)");
+    }
+    fcc_fp32_batch_kernel<KH, RS><<<grid, max_compute_warps(KH) * 32, smem, st>>>(bp);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "fcc_fp32_batch_kernel launch");
+}
+
+template <int KH>
+fcc_status_t launch_batch_kh(int rs, const BatchParams &bp, int grid, size_t smem, cudaStream_t st)
+{
+    switch (rs) {
+    case 1: return launch_batch_inst<KH, 1>(bp, grid, smem, st);
+    case 2: return launch_batch_inst<KH, 2>(bp, grid, smem, st);
+    case 4: return launch_batch_inst<KH, 4>(bp, grid, smem, st);
+    case 8: return launch_batch_inst<KH, 8>(bp, grid, smem, st);
+    default: return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
+    }
+}
+}  // namespace
+
+// One persistent launch of the batched kernel for the (kh, rs) class.  `smem` =
+// kBatchHeaderBytes + the largest layout of the class's plans.  grid = 0 only
+// prepares the kernel (call once per device before capturing a launch).
+fcc_status_t launch_fp32_batch(int kh, int rs, const BatchParams &bp, int grid, size_t smem, cudaStream_t st)
+{
+    switch (kh) {
+    case 2: return launch_batch_kh<2>(rs, bp, grid, smem, st);
+    case 4: return launch_batch_kh<4>(rs, bp, grid, smem, st);
+    case 6: return launch_batch_kh<6>(rs, bp, grid, smem, st);
+    case 8: return launch_batch_kh<8>(rs, bp, grid, smem, st);
+    default: return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    }
+}
+
+int fp32_row_slots(int Q) { return Q <= 32 ? 1 : Q / 32; }
 
 }  // namespace fcc

@@ -67,6 +67,11 @@ struct Fp32Geometry {
     size_t smem_bytes;
 };
 
+inline bool same_geometry(const Fp32Geometry &a, const Fp32Geometry &b)
+{
+    return a.C == b.C && a.GW == b.GW && a.G == b.G && a.F == b.F && a.S == b.S;
+}
+
 // Kernel parameters of the FP32 path (passed by value).
 struct Fp32Params {
     const float2 *spectra;  // [T][M][B]
@@ -88,6 +93,25 @@ struct Fp32Params {
     float *out_corr;        // nullable, [T][P][I]
     unsigned *err;
 };
+
+// Batched FP32 form: one job = a run of consecutive tiles of one plan.
+struct BatchJob {
+    int array;    // index into BatchParams::arrays
+    int tile0;    // first tile (F frames each, F from the array's geometry)
+    int n_tiles;
+};
+
+struct BatchParams {
+    const Fp32Params *arrays;  // [n_arrays], device
+    const BatchJob *jobs;      // [n_jobs], device, in the order CTAs take them
+    int n_jobs;
+    int *counter;              // next job; zeroed before every launch
+};
+
+// Shared-memory header of the batched kernel (the job's Fp32Params and the job
+// index) in front of the plan's own layout.
+constexpr int kBatchHeaderBytes = 256;
+static_assert(sizeof(Fp32Params) + 8 <= kBatchHeaderBytes, "batch header");
 
 // Kernel parameters of the tensor-core (BF16 / FP16) path.
 struct TcParams {
@@ -150,6 +174,14 @@ fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, co
                                const std::vector<double> &Je, const std::vector<double> &Jo, int K_req,
                                double energy);
 fcc_status_t choose_fp32_geometry(fcc_plan *plan);
+fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out);
+// Set the plan's FP32 geometry and rebuild its device tables for it.
+fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g);
+Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                            float *tau, float *coef, float *corr, unsigned *err);
+fcc_status_t launch_fp32_batch(int kh, int rs, const BatchParams &bp, int grid, size_t smem, cudaStream_t st);
+int fp32_threads(int kh);
+int fp32_row_slots(int Q);
 fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,
                          float *peak, float *tau, float *coef, float *corr, cudaStream_t st);
 fcc_status_t prepare_tc(fcc_plan *plan);

@@ -18,6 +18,7 @@
 // dictionary for the kernels.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <numeric>
 
@@ -162,7 +163,61 @@ void launch_basis_kernels(const fcc_plan_info_t &in, double *d_Ae, double *d_Ao,
 
 }  // namespace
 
+// Process-wide cache of finished bases: the bases depend only on N, the lag
+// grid and the K rule (not on the array geometry or fs), so plans that share a
+// key -- e.g. the arrays of a batch -- share one construction.
+struct BasisKey {
+    int dev, N, I, den, K_req;
+    double energy;
+    bool operator<(const BasisKey &o) const
+    {
+        if (dev != o.dev) return dev < o.dev;
+        if (N != o.N) return N < o.N;
+        if (I != o.I) return I < o.I;
+        if (den != o.den) return den < o.den;
+        if (K_req != o.K_req) return K_req < o.K_req;
+        return energy < o.energy;
+    }
+};
+struct BasisEntry {
+    int K, KE, KO;
+    std::vector<double> s_even, s_odd, Pe, Po, Ue, Uo;
+};
+static std::mutex g_basis_mu;
+static std::map<BasisKey, BasisEntry> g_basis_cache;
+
+static fcc_status_t build_plan_bases_uncached(fcc_plan *plan, int K_req, double energy);
+
 fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
+{
+    fcc_plan_info_t &in = plan->info;
+    const BasisKey key{plan->device, in.N, in.I, in.den, K_req > 0 ? K_req : 0, K_req > 0 ? 0.0 : energy};
+    {
+        std::lock_guard<std::mutex> lk(g_basis_mu);
+        auto it = g_basis_cache.find(key);
+        if (it != g_basis_cache.end()) {
+            const BasisEntry &b = it->second;
+            in.K = b.K;
+            in.K_even = b.KE;
+            in.K_odd = b.KO;
+            plan->s_even = b.s_even;
+            plan->s_odd = b.s_odd;
+            plan->Pe = b.Pe;
+            plan->Po = b.Po;
+            plan->Ue = b.Ue;
+            plan->Uo = b.Uo;
+            return FCC_OK;
+        }
+    }
+    fcc_status_t st = build_plan_bases_uncached(plan, K_req, energy);
+    if (st != FCC_OK) return st;
+    std::lock_guard<std::mutex> lk(g_basis_mu);
+    g_basis_cache[key] = BasisEntry{in.K, in.K_even, in.K_odd, plan->s_even, plan->s_odd,
+                                    plan->Pe, plan->Po, plan->Ue, plan->Uo};
+    return FCC_OK;
+}
+
+static fcc_status_t build_plan_bases_uncached(fcc_plan *plan, int K_req, double energy)
 {
     fcc_plan_info_t &in = plan->info;
     const int I = in.I, Q = in.Q, nE = Q + 1, nO = Q;

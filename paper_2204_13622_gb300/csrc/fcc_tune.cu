@@ -1,0 +1,340 @@
+// fcc_tune.cu -- timing autotuner of the FP32 kernel's launch geometry, with a
+// JSON cache (include/fcc_tune.h).
+#include <algorithm>
+#include <cctype>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "fcc_internal.h"
+#include "fcc_tune.h"
+
+namespace fcc {
+namespace {
+
+// ---------------------------------------------------------------------------
+// The cache file: {"version": 1, "entries": {"<key>": {"C": 4, ...}, ...}}.
+// A small reader for exactly this shape (objects, strings, numbers).
+struct Json {
+    const std::string &s;
+    size_t i = 0;
+    bool ok = true;
+    explicit Json(const std::string &src) : s(src) {}
+    void ws()
+    {
+        while (i < s.size() && std::isspace((unsigned char)s[i])) ++i;
+    }
+    bool eat(char c)
+    {
+        ws();
+        if (i < s.size() && s[i] == c) {
+            ++i;
+            return true;
+        }
+        return false;
+    }
+    std::string str()
+    {
+        ws();
+        std::string out;
+        if (i >= s.size() || s[i] != '"') {
+            ok = false;
+            return out;
+        }
+        for (++i; i < s.size() && s[i] != '"'; ++i) {
+            if (s[i] == '\\' && i + 1 < s.size()) ++i;
+            out += s[i];
+        }
+        if (i >= s.size()) ok = false;
+        ++i;
+        return out;
+    }
+    double num()
+    {
+        ws();
+        const char *b = s.c_str() + i;
+        char *e = nullptr;
+        const double v = std::strtod(b, &e);
+        if (e == b) ok = false;
+        i += (size_t)(e - b);
+        return v;
+    }
+};
+
+using Entry = std::map<std::string, double>;
+
+bool parse_cache(const std::string &text, std::map<std::string, Entry> &out)
+{
+    Json j(text);
+    if (!j.eat('{')) return false;
+    if (j.eat('}')) return true;
+    do {
+        const std::string k = j.str();
+        if (!j.ok || !j.eat(':')) return false;
+        if (k == "entries") {
+            if (!j.eat('{')) return false;
+            if (!j.eat('}')) {
+                do {
+                    const std::string key = j.str();
+                    if (!j.ok || !j.eat(':') || !j.eat('{')) return false;
+                    Entry e;
+                    if (!j.eat('}')) {
+                        do {
+                            const std::string f = j.str();
+                            if (!j.ok || !j.eat(':')) return false;
+                            e[f] = j.num();
+                            if (!j.ok) return false;
+                        } while (j.eat(','));
+                        if (!j.eat('}')) return false;
+                    }
+                    out[key] = e;
+                } while (j.eat(','));
+                if (!j.eat('}')) return false;
+            }
+        } else {
+            j.num();  // "version"
+            if (!j.ok) return false;
+        }
+    } while (j.eat(','));
+    return j.eat('}');
+}
+
+std::string escape(const std::string &s)
+{
+    std::string o;
+    for (char c : s) {
+        if (c == '"' || c == '\\') o += '\\';
+        o += c;
+    }
+    return o;
+}
+
+std::mutex g_cache_mu;
+
+bool read_cache(const std::string &path, std::map<std::string, Entry> &out)
+{
+    std::ifstream f(path);
+    if (!f) return false;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    return parse_cache(ss.str(), out);
+}
+
+bool write_cache(const std::string &path, const std::map<std::string, Entry> &all)
+{
+    const std::string tmp = path + ".tmp." + std::to_string((long long)std::rand());
+    {
+        std::ofstream f(tmp);
+        if (!f) return false;
+        f << "{\n  \"version\": 1,\n  \"entries\": {";
+        bool first = true;
+        for (const auto &kv : all) {
+            f << (first ? "\n" : ",\n") << "    \"" << escape(kv.first) << "\": {";
+            bool f2 = true;
+            for (const auto &fv : kv.second) {
+                char buf[64];
+                std::snprintf(buf, sizeof buf, "%.9g", fv.second);
+                f << (f2 ? "" : ", ") << "\"" << escape(fv.first) << "\": " << buf;
+                f2 = false;
+            }
+            f << "}";
+            first = false;
+        }
+        f << "\n  }\n}\n";
+        if (!f) return false;
+    }
+    return std::rename(tmp.c_str(), path.c_str()) == 0;
+}
+
+std::string tune_key(const fcc_plan *plan)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, plan->device);
+    const fcc_plan_info_t &in = plan->info;
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "fp32|%s|sms=%d|M=%d|N=%d|K=%d+%d|I=%d", prop.name, prop.multiProcessorCount,
+                  in.M, in.N, in.K_even, in.K_odd, in.I);
+    return buf;
+}
+
+// Synthetic spectra for timing: a fixed hash of the element index mapped to
+// [-1, 1) per component (content does not change the kernel's work).
+__global__ void fill_kernel(float *x, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        unsigned long long h = (unsigned long long)k * 0x9E3779B97F4A7C15ull;
+        h ^= h >> 29;
+        h *= 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 32;
+        x[k] = (float)(h & 0xFFFFFF) * (2.0f / 16777216.0f) - 1.0f;
+    }
+}
+
+}  // namespace
+
+// Looks the plan's key up in the cache; on a hit with a geometry that is still
+// a candidate, applies it.  Returns true on a hit.
+bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us)
+{
+    if (path.empty()) return false;
+    std::map<std::string, Entry> all;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (!read_cache(path, all)) return false;
+    }
+    auto it = all.find(tune_key(plan));
+    if (it == all.end()) return false;
+    const Entry &e = it->second;
+    auto get = [&](const char *k) { auto f = e.find(k); return f == e.end() ? -1 : (int)f->second; };
+    std::vector<Fp32Geometry> cand;
+    if (fp32_candidates(plan, cand) != FCC_OK) return false;
+    Fp32Geometry want{get("C"), 0, 0, get("GW"), get("G"), get("F"), get("S"), 0, 0};
+    for (const Fp32Geometry &g : cand)
+        if (same_geometry(g, want)) {
+            if (set_fp32_geometry(plan, g) != FCC_OK) return false;
+            if (us) {
+                auto f = e.find("us_per_frame");
+                *us = f == e.end() ? 0.0 : f->second;
+            }
+            return true;
+        }
+    return false;
+}
+
+fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int max_cand, double *us_out)
+{
+    if (plan->info.prec != FCC_PREC_FP32) return fail(FCC_ERR_INVALID_ARG, "autotune needs an FP32 plan");
+    if (!plan->kh || plan->geo.G == 0) return fail(FCC_ERR_UNSUPPORTED, "no FP32 kernel for this plan");
+    if (!force && tune_from_cache(plan, path, us_out)) return FCC_OK;
+    std::vector<Fp32Geometry> cand;
+    fcc_status_t st = fp32_candidates(plan, cand);
+    if (st != FCC_OK) return st;
+    // distinct launch shapes, best heuristic score first
+    std::vector<Fp32Geometry> uniq;
+    for (const Fp32Geometry &g : cand) {
+        bool dup = false;
+        for (const Fp32Geometry &u : uniq) dup = dup || same_geometry(u, g);
+        if (!dup) uniq.push_back(g);
+        if ((int)uniq.size() >= (max_cand > 0 ? max_cand : 8)) break;
+    }
+    const fcc_plan_info_t &in = plan->info;
+    const size_t frame_bytes = (size_t)in.M * in.B * 8;
+    const long long T = std::max<long long>((256LL << 20) / (long long)frame_bytes, 16LL * plan->num_sms);
+    float *d_x = nullptr, *d_peak = nullptr;
+    int *d_idx = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (s) cudaStreamSynchronize(s);
+        cudaFree(d_x);
+        cudaFree(d_peak);
+        cudaFree(d_idx);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    };
+    cudaError_t e = cudaMalloc(&d_x, (size_t)T * frame_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_idx, (size_t)T * in.P * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_peak, (size_t)T * in.P * sizeof(float));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "autotune workspace");
+    }
+    fill_kernel<<<4 * plan->num_sms, 256, 0, s>>>(d_x, (long long)T * in.M * in.B * 2);
+    const Fp32Geometry orig = plan->geo;
+    double best_us = 1e30;
+    Fp32Geometry best = orig;
+    for (const Fp32Geometry &g : uniq) {
+        st = set_fp32_geometry(plan, g);
+        if (st != FCC_OK) break;
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 4 && st == FCC_OK; ++rep) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess)
+                st = launch_fp32(plan, reinterpret_cast<const float2 *>(d_x), T, d_idx, d_peak, nullptr, nullptr,
+                                 nullptr, s);
+            if (e == cudaSuccess && st == FCC_OK) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess && st == FCC_OK) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess && st == FCC_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess && st == FCC_OK) st = cuda_fail(e, "autotune timing");
+            if (rep > 0) best_ms = std::min(best_ms, ms);  // rep 0 warms up
+        }
+        if (st != FCC_OK) break;
+        const double us = 1e3 * best_ms / (double)T;
+        if (getenv("FCC_DEBUG"))
+            fprintf(stderr, "[fcc tune] C=%d GW=%d G=%d F=%d S=%d: %.5f us/frame\n", g.C, g.GW, g.G, g.F, g.S, us);
+        if (us < best_us) {
+            best_us = us;
+            best = g;
+        }
+    }
+    // device error word of the timing runs (hash inputs are finite: expect 0)
+    unsigned err = 0;
+    if (st == FCC_OK) {
+        e = cudaMemcpy(&err, plan->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemset(plan->d_err, 0, sizeof(unsigned));
+        if (e != cudaSuccess) st = cuda_fail(e, "autotune error word");
+    }
+    cleanup();
+    if (st != FCC_OK) {
+        set_fp32_geometry(plan, orig);
+        return st;
+    }
+    if (err & kErrTimeout) {
+        set_fp32_geometry(plan, orig);
+        return fail(FCC_ERR_TIMEOUT, "a device-side wait expired while tuning");
+    }
+    st = set_fp32_geometry(plan, best);
+    if (st != FCC_OK) return st;
+    if (us_out) *us_out = best_us;
+    if (!path.empty()) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        std::map<std::string, Entry> all;
+        read_cache(path, all);  // a missing or unreadable file starts empty
+        all[tune_key(plan)] = Entry{{"C", best.C},  {"GW", best.GW}, {"G", best.G},
+                                    {"F", best.F},  {"S", best.S},   {"us_per_frame", best_us}};
+        if (!write_cache(path, all)) return fail(FCC_ERR_INVALID_ARG, "cannot write the tuning cache " + path);
+    }
+    return FCC_OK;
+}
+
+std::string tune_cache_path(const char *p)
+{
+    if (p && *p) return p;
+    const char *env = getenv("FCC_TUNE_CACHE");
+    return env ? env : "";
+}
+
+}  // namespace fcc
+
+using namespace fcc;
+
+extern "C" {
+
+fcc_status_t fcc_plan_geometry(const fcc_plan_t *plan, fcc_geometry_t *out)
+{
+    if (!plan || !out) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    const Fp32Geometry &g = plan->geo;
+    *out = fcc_geometry_t{g.C, g.GW, g.G, g.F, g.S, g.G * g.GW * 32, (long long)g.smem_bytes};
+    return FCC_OK;
+}
+
+fcc_status_t fcc_plan_autotune(fcc_plan_t *plan, const char *cache_path, int force, int max_candidates,
+                               double *us_per_frame)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    return tune_fp32(plan, tune_cache_path(cache_path), force != 0, max_candidates, us_per_frame);
+}
+
+}  // extern "C"

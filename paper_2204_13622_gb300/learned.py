@@ -112,12 +112,9 @@ THRESHOLDS = (0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4, 0.45, 0.5, 0.6, 0.7)
 def pick_threshold(mlp, data, grid=THRESHOLDS) -> float:
     """Confidence threshold of the gate with the lowest RMSE on `data` (a
     validation set, not the held-out one)."""
+    import torch
+
     out = mlp.infer(data["features"], data["tau_fcc"], 0.5)
     t, raw, fcc, conf = data["t"], out["raw"], data["tau_fcc"], out["conf"]
-    best = min(grid, key=lambda th: rmse(torch_where(conf >= th, raw, fcc), t))
+    best = min(grid, key=lambda th: rmse(torch.where(conf >= th, raw, fcc), t))
     return float(best)
-
-
-def torch_where(c, a, b):
-    import torch
-    return torch.where(c, a, b)

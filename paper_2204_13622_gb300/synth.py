@@ -268,3 +268,47 @@ def mlp_init_params(n_in: int, hidden: int, seed: int) -> np.ndarray:
         parts.append(rng.uniform(-a, a, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# batched form: many independent arrays
+# ----------------------------------------------------------------------------
+def batched_arrays(n: int, seed: int, mics=(2, 4, 6, 8, 12, 16), aperture=(0.02, 0.08),
+                   Ns=(256, 512, 1024), rates=(16000.0, 48000.0), frames=(64, 4096), lag_den: int = 4):
+    """Seeded descriptions of n independent arrays: per array a microphone count
+    drawn from `mics`, a uniform circular array whose diameter (the aperture) is
+    uniform in `aperture` metres, N from `Ns`, fs from `rates`, T uniform in
+    [frames[0], frames[1]] and the lag grid step 1/lag_den.  Returns a list of
+    dicts (n_mics, fs, N, lag_den, mic_xyz, T, seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for a in range(n):
+        M = int(rng.choice(mics))
+        ap = float(rng.uniform(*aperture))
+        out.append(dict(n_mics=M, fs=float(rng.choice(rates)), N=int(rng.choice(Ns)), lag_den=int(lag_den),
+                        mic_xyz=circular_array(M, ap / 2.0), T=int(rng.integers(frames[0], frames[1] + 1)),
+                        seed=int(rng.integers(0, 2 ** 31))))
+    return out
+
+
+def array_spectra(arr: dict, device="cpu", snr_db=(0.0, 30.0), c: float = SPEED_OF_SOUND):
+    """Spectra [T, M, N/2+1] complex64 of one array from `batched_arrays`: one
+    far-field complex white source from a seeded direction, delayed per
+    microphone by exp(-j 2 pi f delay / N), plus white noise at a seeded SNR."""
+    import torch
+
+    rng = np.random.default_rng(arr["seed"])
+    xyz, fs, N, T = arr["mic_xyz"], arr["fs"], arr["N"], arr["T"]
+    M, B = xyz.shape[0], N // 2 + 1
+    direction = unit_vector(rng.uniform(0, 2 * np.pi), rng.uniform(0, np.pi / 2))
+    d = far_field_delays(xyz, direction, fs, c)
+    snr = rng.uniform(*snr_db)
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(arr["seed"]))
+    f = np.arange(B)
+    ramp = torch.from_numpy(np.exp(-2j * np.pi * np.outer(d, f) / N).astype(np.complex64)).to(dev)
+    src = torch.randn((T, 1, B), dtype=torch.complex64, device=dev, generator=gen)
+    X = torch.randn((T, M, B), dtype=torch.complex64, device=dev, generator=gen)
+    X.mul_(10.0 ** (-snr / 20.0)).add_(src * ramp)
+    return X
