@@ -6,6 +6,11 @@ frame and pair of the workload, with the spectra already resident in HBM.
 Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcc|reference]
+                  [--workload circle8|grid16|square4|batched|learned]
+
+The default line is the 8-mic circle.  --workload batched times 4096
+independent arrays under one CUDA graph; --workload learned trains and
+evaluates the learned head (RMSE in samples).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores.  Under torchrun every rank runs its own 2^20 frames
@@ -343,6 +348,145 @@ def run_fcc(args, rank, world, local):
     return res
 
 
+def _peak_hbm():
+    f = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(f):
+        return float(json.load(open(f)).get("hbm_gbs", 6800.0)), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback"
+
+
+def run_batched(args, rank, world, local):
+    """Batched form: 4096 independent arrays (mixed M, aperture, N, fs, T) in
+    per-class persistent launches captured in one CUDA graph; one step = one
+    graph launch over every frame and pair of every array."""
+    import numpy as np
+    import torch
+
+    from paper_2204_13622_gb300 import binding, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    distributed = dist_init(world, "nccl")
+    arrs = synth.batched_arrays(args.arrays, seed=4 + 7919 * rank)
+    t0 = time.perf_counter()
+    cache = os.environ.get("FCC_TUNE_CACHE") or os.path.join("/tmp", f"fcc_tune_{os.getpid()}.json")
+    batch = binding.Batch(arrs, device=local, autotune=args.autotune, tune_cache=cache)
+    t_create = time.perf_counter() - t0
+    info = batch.info()
+    need = info["spectra_bytes"] + 1.5 * info["pair_frames"] * 12
+    free, _ = torch.cuda.mem_get_info(dev)
+    if need > 0.97 * free:
+        raise RuntimeError(f"batched workload needs {need / 1e9:.1f} GB, {free / 1e9:.1f} GB free")
+    X = [synth.array_spectra(a, device=dev) for a in arrs]
+    out = batch.outputs(tau_hat=True)
+    batch.bind(X, out)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        batch.run(stream)
+    batch.sync(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(distributed)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            batch.run(stream)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(distributed)
+    batch.sync(stream)
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = sum(per) / args.steps
+    ms_max = max_over_ranks(ms, distributed, dev)
+    value = world * info["pair_frames"] / (ms_max / 1000.0)
+    bytes_per_step = info["spectra_bytes"] + info["result_bytes"]
+    achieved = bytes_per_step / (ms / 1000.0) / 1e9
+    peak, psrc = _peak_hbm()
+    res = None
+    if rank == 0:
+        # accuracy: 8 arrays x 16 frames against the FP64 oracle; CPU baseline:
+        # the oracle on the same sample
+        from oracle import oracle as O
+        agree, n_pf, t_or = [], 0, 0.0
+        for a in np.linspace(0, len(arrs) - 1, 8).astype(int):
+            inf = batch.arrays[a]
+            basis = O.Basis(inf["N"], inf["L"], inf["den"], K=inf["K"])
+            Xs = X[a][:16].cpu().numpy()
+            t1 = time.perf_counter()
+            idx, _, _, y = O.tdoa(Xs, basis.WK, basis.taus, basis.delta, want_y=True)
+            t_or += time.perf_counter() - t1
+            n_pf += idx.size
+            agree.append((out[a]["lag_idx"][:16].cpu().numpy() == idx).astype(np.float64).ravel())
+        agree = np.concatenate(agree)
+        res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"batched: {args.arrays} arrays, M in {{2,4,6,8,12,16}}, aperture 2-8 cm, "
+                                      "N in {256,512,1024}, fs in {16,48} kHz, 64-4096 frames each",
+                          "arrays": info["n_arrays"], "frames": info["frames"], "pair_frames": info["pair_frames"],
+                          "classes": info["n_classes"], "jobs": info["n_jobs"], "bases": info["n_bases"],
+                          "autotune": bool(args.autotune), "create_s": round(t_create, 2),
+                          "l2": f"inputs ({info['spectra_bytes'] / 1e9:.1f} GB) larger than L2; no flush"},
+               "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": None, "kernel": "fcc_fp32_batch_kernel",
+                            "bytes_per_launch": bytes_per_step, "peak_source": psrc},
+               "accuracy_vs_oracle": {"pair_frames": int(n_pf), "argmax_agreement": float(agree.mean())},
+               "cpu_baseline": {"value": n_pf / t_or, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                                "sample": f"16 frames of 8 arrays ({n_pf} pair-frames), FP64 C oracle"},
+               "e2e": None, "gpu_launches": args.steps * info["n_classes"],
+               "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
+    batch.close()
+    return res
+
+
+def run_learned(args, rank, world, local):
+    """Learned head: train on FCC coefficients of synthetic pair-frames with the
+    library's kernels, report held-out TDoA RMSE against FCC + parabola and the
+    head's training / inference throughput."""
+    import torch
+
+    from paper_2204_13622_gb300 import learned
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    plan = learned.pair_plan(device=local)
+    t0 = time.perf_counter()
+    tr = learned.make_dataset(plan, args.train, seed=101, tau_max=4.66, device=dev)
+    va = learned.make_dataset(plan, 1 << 18, seed=303, tau_max=4.66, device=dev)
+    te = learned.make_dataset(plan, args.heldout, seed=202, tau_max=4.66, device=dev)
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    mlp = learned.new_head(2 * plan.K, learned.feature_scale(tr["features"]), seed=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = learned.train(mlp, tr, epochs=args.epochs, batch=4096)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    train_s = e0.elapsed_time(e1) / 1000.0
+    th = learned.pick_threshold(mlp, va)
+    r = learned.evaluate(mlp, te, th)
+    # inference throughput (gated forward over the held-out set)
+    outb = {k: torch.empty(te["t"].numel(), device=dev) for k in ("tau", "conf", "raw")}
+    for _ in range(3):
+        mlp.infer(te["features"], te["tau_fcc"], th, out=outb)
+    e0.record()
+    for _ in range(args.steps):
+        mlp.infer(te["features"], te["tau_fcc"], th, out=outb)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    inf_ms = e0.elapsed_time(e1) / args.steps
+    res = {"metric": "learned-head TDoA RMSE (samples) vs FCC + parabolic refinement", "unit": "samples",
+           "value": r["rmse_mlp_gated"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+           "warmup": 3, "dtype": "bf16 weights, f32 accumulate", "data": "synthetic", "vs_baseline": None,
+           "config": {"workload": "learned: 2 mics, N=512, grid [-5, 5] step 1/4 (I=41), K=%d, tau_max 4.66, "
+                                  "SNR U[-5, 30] dB" % plan.K, "train_pair_frames": args.train,
+                      "heldout_pair_frames": args.heldout, "epochs": args.epochs, "batch": 4096},
+           "rmse": r, "threshold": th, "loss_per_epoch": [round(x, 5) for x in hist],
+           "train_samples_per_s": args.epochs * (args.train // 4096) * 4096 / train_s,
+           "infer_pair_frames_per_s": te["t"].numel() / (inf_ms / 1000.0), "data_s": round(t_data, 1)}
+    mlp.close()
+    plan.close()
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,8 +495,14 @@ def main(argv=None):
     ap.add_argument("--impl", default="fcc", choices=["fcc", "reference"])
     ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
     ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
-    ap.add_argument("--workload", default="circle8", choices=["circle8", "grid16", "square4"])
+    ap.add_argument("--workload", default="circle8",
+                    choices=["circle8", "grid16", "square4", "batched", "learned"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
+    ap.add_argument("--autotune", action="store_true", help="batched: time the tile shapes first")
+    ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")
+    ap.add_argument("--heldout", type=int, default=1_000_000, help="learned: held-out pair-frames")
+    ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -360,7 +510,12 @@ def main(argv=None):
     else:
         import __graft_entry__ as g
         g.build() if rank == 0 and world == 1 else None
-        res = run_fcc(args, rank, world, local)
+        if args.workload == "batched":
+            res = run_batched(args, rank, world, local)
+        elif args.workload == "learned":
+            res = run_learned(args, rank, world, local) if rank == 0 else None
+        else:
+            res = run_fcc(args, rank, world, local)
     if res is not None:
         print(json.dumps(res), flush=True)
 

@@ -292,7 +292,7 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
             return st;
         }
     }
-    if (getenv("FCC_DEBUG"))
+    if (debug_enabled())
         fprintf(stderr, "[fcc] plan M=%d N=%d I=%d K=%d (%d+%d) kh=%d slots=%d fp32: C=%d SB=%d GW=%d G=%d F=%d S=%d smem=%zu\n",
                 in.M, in.N, in.I, in.K, in.K_even, in.K_odd, p->kh, p->n_slots, p->geo.C, p->geo.SB, p->geo.GW,
                 p->geo.G, p->geo.F, p->geo.S, p->geo.smem_bytes);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,13 @@ enum : unsigned {
 // Records a detail message for fcc_last_error() and returns `st`.
 fcc_status_t fail(fcc_status_t st, const std::string &msg);
 fcc_status_t cuda_fail(cudaError_t e, const char *what);
+
+// FCC_DEBUG set to anything but "" or "0": print plan geometry and tuning steps.
+inline bool debug_enabled()
+{
+    const char *d = std::getenv("FCC_DEBUG");
+    return d && *d && !(d[0] == '0' && d[1] == 0);
+}
 
 // Makes `dev` current for the scope of one entry point and restores the
 // caller's device afterwards.

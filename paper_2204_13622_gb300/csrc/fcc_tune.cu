@@ -270,7 +270,7 @@ fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int 
         }
         if (st != FCC_OK) break;
         const double us = 1e3 * best_ms / (double)T;
-        if (getenv("FCC_DEBUG"))
+        if (debug_enabled())
             fprintf(stderr, "[fcc tune] C=%d GW=%d G=%d F=%d S=%d: %.5f us/frame\n", g.C, g.GW, g.G, g.F, g.S, us);
         if (us < best_us) {
             best_us = us;
