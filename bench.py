@@ -499,7 +499,8 @@ def main(argv=None):
                     choices=["circle8", "grid16", "square4", "batched", "learned"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
-    ap.add_argument("--autotune", action="store_true", help="batched: time the tile shapes first")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="batched: keep the heuristic tile shapes (default: autotuned)")
     ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")
     ap.add_argument("--heldout", type=int, default=1_000_000, help="learned: held-out pair-frames")
     ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")

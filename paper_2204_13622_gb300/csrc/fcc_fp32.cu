@@ -576,7 +576,7 @@ fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &ou
     const int BS = ((2 * kh / 4) % 2 == 0) ? 2 * kh + 4 : 2 * kh;
     const int maxw = max_compute_warps(kh);
     std::vector<std::pair<double, Fp32Geometry>> scored;
-    for (int C = 4; C <= 16 && C <= in.Q; C <<= 1) {
+    for (int C = 4; C <= 32 && C <= in.Q; C <<= 1) {
         const int SB = 32 / C;
         const int nb = (n_slots + SB - 1) / SB;
         const double util = (double)n_slots / (nb * SB);
@@ -591,7 +591,8 @@ fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &ou
                     // one frame each beat 6 pairs of warps with double-buffered
                     // stages by 1.4x); fewer chunks mean a shorter shuffle
                     // reduction; a second stage per group only breaks ties
-                    const double score = util * (G * GW) * (1.0 - 0.1 * (C / 4 - 1)) + (Sg >= 2 ? 0.01 : 0.0);
+                    const double score =
+                        util * (G * GW) * (1.0 - 0.1 * std::log2((double)C / 4.0)) + (Sg >= 2 ? 0.01 : 0.0);
                     scored.push_back({score, Fp32Geometry{C, SB, nb * 32, GW, G, F, S, BS, L.total}});
                 }
             }
