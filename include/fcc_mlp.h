@@ -91,13 +91,19 @@ fcc_status_t fcc_mlp_train_step(fcc_mlp_t *mlp, const float *d_features, const f
                                 void *stream);
 
 /*
- * Forward with the confidence gate: d_tau[s] = y0 if sigmoid(y1) >= threshold,
+ * Forward on the tensor cores (tcgen05, BF16 weights, activations entered as a
+ * two-term BF16 split, FP32 accumulation in tensor memory) with the confidence
+ * gate: d_tau[s] = y0 if sigmoid(y1) >= threshold,
  * else d_tau_fcc[s] (d_tau_fcc NULL: always y0).  d_conf[s] = sigmoid(y1) and
  * d_raw[s] = y0 are written when not NULL.  n = 0 is a no-op (any pointers).
  * Errors: INVALID_ARG, CUDA.
  */
 fcc_status_t fcc_mlp_infer(fcc_mlp_t *mlp, const float *d_features, const float *d_tau_fcc, long long n,
                            float threshold, float *d_tau, float *d_conf, float *d_raw, void *stream);
+
+/* Synchronise `stream`, then read and clear the head's device error word
+ * (FCC_OK or FCC_ERR_TIMEOUT from a bounded wait of the inference kernel). */
+fcc_status_t fcc_mlp_sync(fcc_mlp_t *mlp, void *stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc",
            # include/fcc_mlp.h
            "fcc_mlp_num_params", "fcc_mlp_create", "fcc_mlp_destroy", "fcc_mlp_get_state",
-           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer",
+           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer", "fcc_mlp_sync",
            # include/fcc_tune.h
            "fcc_plan_geometry", "fcc_plan_autotune",
            # include/fcc_batch.h
@@ -112,6 +112,7 @@ def lib():
         L.fcc_mlp_gradient.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
         L.fcc_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp]
         L.fcc_mlp_infer.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp, _vp, _vp]
+        L.fcc_mlp_sync.argtypes = [_vp, _vp]
         L.fcc_plan_geometry.argtypes = [_vp, ctypes.POINTER(Geometry)]
         L.fcc_plan_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, _dp]
         L.fcc_batch_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
@@ -128,7 +129,7 @@ def lib():
                      "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_mlp_create", "fcc_mlp_get_state", "fcc_mlp_set_state", "fcc_mlp_gradient",
-                     "fcc_mlp_train_step", "fcc_mlp_infer"):
+                     "fcc_mlp_train_step", "fcc_mlp_infer", "fcc_mlp_sync"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_plan_create", "fcc_plan_info", "fcc_plan_taus", "fcc_plan_singular_values",
                      "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa", "fcc_plan_sync",
@@ -392,6 +393,11 @@ class MLP:
         self._check(feat, tau_true, tau_fcc)
         check(lib().fcc_mlp_train_step(self._h, _ptr(feat), _ptr(tau_true), _ptr(tau_fcc), feat.shape[0],
                                        float(lr), _ptr(loss), _stream(stream, feat.device)), "fcc_mlp_train_step")
+
+    def sync(self, stream=None):
+        """Synchronise and raise if the inference kernel latched a timeout."""
+        import torch
+        check(lib().fcc_mlp_sync(self._h, _stream(stream, torch.device("cuda", self.device))), "fcc_mlp_sync")
 
     def infer(self, feat, tau_fcc=None, threshold: float = 0.5, stream=None, out=None):
         """dict(tau, conf, raw) of device tensors [n]."""

@@ -12,8 +12,8 @@
 //   mlp_reduce_kernel sums the per-block partials in a fixed order (bitwise
 //                     reproducible gradients);
 //   mlp_adam_kernel   Adam on the FP32 masters, refreshing the BF16 copies;
-//   mlp_infer_kernel  forward + confidence gate: TDoA = y0 when sigmoid(y1) >=
-//                     threshold, else the plain FCC estimate.
+//   mlp_infer_tc_kernel  forward on the tensor cores + confidence gate: TDoA =
+//                     y0 when sigmoid(y1) >= threshold, else the plain FCC estimate.
 // Loss (mean over the batch): (y0 - t)^2 + lambda * BCE(sigmoid(y1), g), with the
 // target g = [|y0 - t| <= |t_fcc - t|]: the confidence learns when the network
 // beats the plain argmax + parabola.
@@ -23,6 +23,7 @@
 #include <new>
 #include <vector>
 
+#include "fcc_device.cuh"
 #include "fcc_internal.h"
 #include "fcc_mlp.h"
 
@@ -278,28 +279,209 @@ __global__ void mlp_adam_kernel(float *p, const float *g, float *m, float *v, lo
     }
 }
 
-__global__ void __launch_bounds__(kH) mlp_infer_kernel(MlpW w, const float *feat, const float *tau_fcc, long long n,
-                                                       float threshold, float *tau_out, float *conf_out, float *raw_out)
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores.  One CTA of 128 threads takes 128-sample tiles
+// (thread = sample = TMEM lane).  Layer 1 and layer 2 are tcgen05.mma
+// (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128, N = 128); the activations
+// enter as a two-term BF16 split a = hi + lo (hi = bf16(a), lo = bf16(a - hi)),
+// so each layer is two MMA passes against the same BF16 weights and the
+// products carry the activations to about 2^-17 -- the FP32 activations of the
+// training kernels.  The epilogues read TMEM with tcgen05.ld (bias, exact-erf
+// GELU, the split for the next layer; layer 3 and the gate on the CUDA cores).
+constexpr int kTcRows = 128;
+
+struct TcMlpLayout {
+    int K1;  // layer-1 K: n_in padded to a multiple of 16
+    size_t w1, w2, abuf, w3, b1, b2, total;
+};
+
+__host__ __device__ inline TcMlpLayout tc_mlp_layout(int nin)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
-    load_weights(s, w);
-    __syncthreads();
-    const long long n_tiles = (n + kTileS - 1) / kTileS;
-    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const long long base = t * kTileS;
-        const int ns = (int)min((long long)kTileS, n - base);
-        load_x(s, feat, base, ns, w.nin);
-        forward_tile(s, w.nin, false);
-        if (threadIdx.x < ns) {
-            const int r = threadIdx.x;
-            const float y0 = s.Y[r][0], c = 1.f / (1.f + expf(-s.Y[r][1]));
-            tau_out[base + r] = (c >= threshold || !tau_fcc) ? y0 : tau_fcc[base + r];
-            if (conf_out) conf_out[base + r] = c;
-            if (raw_out) raw_out[base + r] = y0;
-        }
-        __syncthreads();
+    TcMlpLayout L;
+    L.K1 = (nin + 15) / 16 * 16;
+    size_t o = 128;                       // mbarrier, TMEM address, abort flag
+    L.w1 = o;
+    o += (size_t)kH * L.K1 * 2;           // B of layer 1: [128][K1] bf16, K-major core matrices
+    L.w2 = o;
+    o += (size_t)kH * kH * 2;             // B of layer 2: [128][128]
+    L.abuf = o;
+    o += (size_t)kTcRows * 2 * kH * 2;    // A of layer 2: [128][hi 128 | lo 128]; A of layer 1 aliases it
+    L.w3 = o;
+    o += 2 * kH * 4;
+    L.b1 = o;
+    o += kH * 4;
+    L.b2 = o;
+    o += kH * 4 + 16;
+    L.total = o;
+    return L;
+}
+
+// Byte offset of element (r, k) of a K-major operand with K columns (bf16):
+// 8-row x 16-byte core matrices, adjacent along K, then along rows.
+__device__ __forceinline__ int kmaj(int r, int k, int K) { return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+__device__ __forceinline__ uint32_t bf2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Write 8 consecutive K entries of row r (hi part at k, lo part at k + koff).
+__device__ __forceinline__ void store_split8(unsigned char *A, int r, int k, int K, int koff, const float *v)
+{
+    float hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        hi[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+        lo[j] = v[j] - hi[j];
     }
+    *reinterpret_cast<uint4 *>(A + kmaj(r, k, K)) =
+        make_uint4(bf2(hi[0], hi[1]), bf2(hi[2], hi[3]), bf2(hi[4], hi[5]), bf2(hi[6], hi[7]));
+    *reinterpret_cast<uint4 *>(A + kmaj(r, k + koff, K)) =
+        make_uint4(bf2(lo[0], lo[1]), bf2(lo[2], lo[3]), bf2(lo[4], lo[5]), bf2(lo[6], lo[7]));
+}
+
+__global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const float *feat, const float *tau_fcc,
+                                                               long long n, float threshold, float *tau_out,
+                                                               float *conf_out, float *raw_out, unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nin = w.nin;
+    const TcMlpLayout L = tc_mlp_layout(nin);
+    const int K1 = L.K1;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 8);
+    int *abort_flag = reinterpret_cast<int *>(smem + 12);
+    unsigned char *W1s = smem + L.w1, *W2s = smem + L.w2, *A = smem + L.abuf;
+    float *W3s = reinterpret_cast<float *>(smem + L.w3), *b1s = reinterpret_cast<float *>(smem + L.b1),
+          *b2s = reinterpret_cast<float *>(smem + L.b2);
+    const int r = threadIdx.x, warp = r >> 5;
+
+    // weights into shared memory, once per CTA
+    for (int e = r; e < kH * K1; e += blockDim.x) {
+        const int o = e / K1, k = e % K1;
+        *reinterpret_cast<__nv_bfloat16 *>(W1s + kmaj(o, k, K1)) =
+            k < nin ? w.W1[o * nin + k] : __float2bfloat16_rn(0.f);
+    }
+    for (int e = r; e < kH * kH; e += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16 *>(W2s + kmaj(e / kH, e % kH, kH)) = w.W2[e];
+    for (int e = r; e < 2 * kH; e += blockDim.x) W3s[e] = __bfloat162float(w.W3[e]);
+    b1s[r] = w.b1[r];
+    b2s[r] = w.b2[r];
+    const float b30 = w.b3[0], b31 = w.b3[1];
+    float sc[kMaxIn];
+#pragma unroll
+    for (int k = 0; k < kMaxIn; ++k) sc[k] = k < nin ? w.scale[k] : 0.f;
+    if (r == 0) {
+        mbar_init(bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(kH));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    // instruction descriptor: D FP32, A and B BF16, K-major, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    const uint32_t a_addr = smem_u32(A), w1_addr = smem_u32(W1s), w2_addr = smem_u32(W2s);
+    unsigned phase = 0;
+    bool failed = false;
+
+    // one MMA pass set, committed to the barrier; every thread waits for it
+    auto mma_and_wait = [&](int layer) -> bool {
+        fence_proxy_async();  // our generic stores of A -> the tensor cores' reads
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (r == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (layer == 1) {
+                const uint32_t sbo_a = (uint32_t)(2 * K1 / 8) * 128, sbo_b = (uint32_t)(K1 / 8) * 128;
+                for (int j = 0; j < 2 * K1 / 16; ++j)
+                    umma_f16(tmem, umma_desc(a_addr + j * 256, 128, sbo_a),
+                             umma_desc(w1_addr + (j % (K1 / 16)) * 256, 128, sbo_b), idesc, j > 0);
+            } else {
+                const uint32_t sbo_a = (uint32_t)(2 * kH / 8) * 128, sbo_b = (uint32_t)(kH / 8) * 128;
+                for (int j = 0; j < 2 * kH / 16; ++j)
+                    umma_f16(tmem, umma_desc(a_addr + j * 256, 128, sbo_a),
+                             umma_desc(w2_addr + (j % (kH / 16)) * 256, 128, sbo_b), idesc, j > 0);
+            }
+            umma_commit(bar);
+        }
+        const bool ok = mbar_wait(bar, phase);
+        phase ^= 1u;
+        if (!ok) atomicOr(abort_flag, 1);
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return *abort_flag == 0;
+    };
+
+    const long long n_tiles = (n + kTcRows - 1) / kTcRows;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const long long s = t * kTcRows + r;
+        const bool live = s < n;
+        // ---- A of layer 1: scaled features, split into hi | lo
+        {
+            float x[kMaxIn];
+#pragma unroll
+            for (int k = 0; k < kMaxIn; ++k) x[k] = (live && k < nin) ? feat[(size_t)s * nin + k] * sc[k] : 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxIn; k += 8)
+                if (k < K1) store_split8(A, r, k, 2 * K1, K1, x + k);
+        }
+        if (!mma_and_wait(1)) {
+            failed = true;
+            break;
+        }
+        // ---- epilogue 1: bias, GELU, split into the A of layer 2
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tmem_ld32(t_row + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1s[c0 + j]);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) store_split8(A, r, c0 + j, 2 * kH, kH, v + j);
+        }
+        if (!mma_and_wait(2)) {
+            failed = true;
+            break;
+        }
+        // ---- epilogue 2: bias, GELU, layer 3, gate
+        float y0 = b30, y1 = b31;
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            float v[32];
+            tmem_ld32(t_row + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float h = gelu(v[j] + b2s[c0 + j]);
+                y0 = fmaf(W3s[c0 + j], h, y0);
+                y1 = fmaf(W3s[kH + c0 + j], h, y1);
+            }
+        }
+        if (live) {
+            const float c = 1.f / (1.f + expf(-y1));
+            tau_out[s] = (c >= threshold || !tau_fcc) ? y0 : tau_fcc[s];
+            if (conf_out) conf_out[s] = c;
+            if (raw_out) raw_out[s] = y0;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // TMEM and A are free for the next tile
+    }
+    if (failed) {
+        if (r == 0) atomicOr(err, kErrTimeout);
+        // the last MMAs may still be running: wait once more (bounded) before freeing TMEM
+        if (!mbar_wait(bar, phase ^ 1u) && r == 0) atomicOr(err, kErrTimeout);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kH));
 }
 
 __global__ void bf16_copy_kernel(const float *src, __nv_bfloat16 *dst, long long n)
@@ -320,6 +502,7 @@ struct fcc_mlp {
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
     __nv_bfloat16 *Wb = nullptr;  // W1, W2, W3 BF16 copies, contiguous
     float *partial = nullptr, *loss_partial = nullptr;
+    unsigned *d_err = nullptr;  // device error word (bounded waits of the inference kernel)
     int nb = 0;
 };
 
@@ -411,6 +594,8 @@ fcc_status_t fcc_mlp_create(int n_in, int hidden, const float *h_in_scale, doubl
     if (e == cudaSuccess) e = cudaMalloc(&h->partial, (size_t)h->nb * np_ * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->loss_partial, (size_t)h->nb * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->scale, (size_t)n_in * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(unsigned));
     if (e == cudaSuccess) {
         std::vector<float> sc(n_in, 1.f);
         if (h_in_scale) sc.assign(h_in_scale, h_in_scale + n_in);
@@ -445,6 +630,7 @@ void fcc_mlp_destroy(fcc_mlp_t *h)
     cudaFree(h->partial);
     cudaFree(h->loss_partial);
     cudaFree(h->scale);
+    cudaFree(h->d_err);
     delete h;
 }
 
@@ -519,18 +705,33 @@ fcc_status_t fcc_mlp_infer(fcc_mlp_t *h, const float *d_feat, const float *d_tau
     if (n == 0) return FCC_OK;
     if (!d_feat || !d_tau) return fail(FCC_ERR_INVALID_ARG, "null argument");
     DeviceScope scope(h->device);
+    const size_t smem = tc_mlp_layout(h->nin).total;
     static bool attr[64] = {};
     if (!attr[h->device & 63]) {
-        FCC_CUDA_TRY(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(MlpSmem)));
+        FCC_CUDA_TRY(cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_mlp_layout(kMaxIn).total));  // the largest layout
         attr[h->device & 63] = true;
     }
-    const long long tiles = (n + kTileS - 1) / kTileS;
+    const long long tiles = (n + kTcRows - 1) / kTcRows;
     const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * 2);
-    mlp_infer_kernel<<<grid, kH, sizeof(MlpSmem), static_cast<cudaStream_t>(stream)>>>(
-        weights(h), d_feat, d_tau_fcc, n, threshold, d_tau, d_conf, d_raw);
+    mlp_infer_tc_kernel<<<grid, kTcRows, smem, static_cast<cudaStream_t>(stream)>>>(
+        weights(h), d_feat, d_tau_fcc, n, threshold, d_tau, d_conf, d_raw, h->d_err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp inference");
+}
+
+fcc_status_t fcc_mlp_sync(fcc_mlp_t *h, void *stream)
+{
+    if (!h) return fail(FCC_ERR_INVALID_ARG, "null mlp");
+    DeviceScope scope(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FCC_CUDA_TRY(cudaStreamSynchronize(st));
+    unsigned err = 0;
+    FCC_CUDA_TRY(cudaMemcpyAsync(&err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    FCC_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), st));
+    FCC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (err & kErrTimeout) return fail(FCC_ERR_TIMEOUT, "a device-side wait expired");
+    return FCC_OK;
 }
 
 }  // extern "C"

@@ -102,9 +102,11 @@ def test_gradient_matches_oracle(B, O, n, nin):
     mlp.close()
 
 
-def test_forward_and_gate_match_oracle(B, O):
-    n, nin = 3001, 16
-    p = synth.mlp_init_params(nin, H, seed=5)
+@pytest.mark.parametrize("n,nin", [(3001, 16), (100000, 16), (777, 5), (2048, 32)])
+def test_forward_and_gate_match_oracle(B, O, n, nin):
+    # inference runs on the tensor cores: BF16 weights, activations split into
+    # two BF16 terms (about 2^-17 relative), FP32 accumulation
+    p = synth.mlp_init_params(nin, H, seed=5 + nin)
     feat, scale, x, t, tfcc = _inputs(O, n, nin, 7, p)
     mlp = B.MLP(nin, p, in_scale=scale)
     f_d, c_d = _dev(feat, tfcc)
@@ -125,6 +127,7 @@ def test_forward_and_gate_match_oracle(B, O):
     # threshold 0 / above 1: all head / all fallback
     assert np.array_equal(mlp.infer(f_d, c_d, 0.0)["tau"].cpu().numpy(), out["raw"].cpu().numpy())
     assert np.array_equal(mlp.infer(f_d, c_d, 1.5)["tau"].cpu().numpy(), tfcc)
+    mlp.sync()
     mlp.close()
 
 
