@@ -480,6 +480,33 @@ def run_learned(args, rank, world, local):
     e1.record()
     torch.cuda.synchronize(dev)
     inf_ms = e0.elapsed_time(e1) / args.steps
+    # FCC then the head on the 8-mic circle workload (its grid is the pair grid
+    # the head was trained on): pair-frames/s through fcc_tdoa_learned
+    from paper_2204_13622_gb300 import binding, workloads
+    w = workloads.CIRCLE8
+    frames = args.frames or w.T
+    Xc = w.spectra(T=frames, device=dev, seed=2)
+    plan8 = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local)
+    if plan8.K != plan.K:
+        raise RuntimeError("the circle's grid gives a different K than the pair grid")
+    lo = plan8.tdoa_learned(Xc, mlp, th)
+    for _ in range(3):
+        plan8.tdoa_learned(Xc, mlp, th, out=lo)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        plan8.tdoa_learned(Xc, mlp, th, out=lo)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    plan8.sync()
+    mlp.sync()
+    c8_ms = e0.elapsed_time(e1) / args.steps
+    c8 = {"workload": w.name if frames == w.T else f"{w.name} truncated to {frames} frames",
+          "ms_per_step": c8_ms, "pair_frames_per_s": frames * w.P / (c8_ms / 1000.0),
+          "head_share_of_pair_frames": float((lo["conf"] >= th).float().mean()),
+          "kernels": "fcc_fp32_kernel (with coefficients) + mlp_infer_tc_kernel"}
+    del Xc, lo
+    plan8.close()
     res = {"metric": "learned-head TDoA RMSE (samples) vs FCC + parabolic refinement", "unit": "samples",
            "value": r["rmse_mlp_gated"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
            "warmup": 3, "dtype": "bf16 weights, f32 accumulate", "data": "synthetic", "vs_baseline": None,
@@ -488,7 +515,8 @@ def run_learned(args, rank, world, local):
                       "heldout_pair_frames": args.heldout, "epochs": args.epochs, "batch": 4096},
            "rmse": r, "threshold": th, "loss_per_epoch": [round(x, 5) for x in hist],
            "train_samples_per_s": args.epochs * (args.train // 4096) * 4096 / train_s,
-           "infer_pair_frames_per_s": te["t"].numel() / (inf_ms / 1000.0), "data_s": round(t_data, 1)}
+           "infer_pair_frames_per_s": te["t"].numel() / (inf_ms / 1000.0), "data_s": round(t_data, 1),
+           "fcc_then_head": c8}
     mlp.close()
     plan.close()
     return res

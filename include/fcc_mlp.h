@@ -101,6 +101,20 @@ fcc_status_t fcc_mlp_train_step(fcc_mlp_t *mlp, const float *d_features, const f
 fcc_status_t fcc_mlp_infer(fcc_mlp_t *mlp, const float *d_features, const float *d_tau_fcc, long long n,
                            float threshold, float *d_tau, float *d_conf, float *d_raw, void *stream);
 
+/*
+ * FCC followed by the learned head on every pair-frame: fcc_tdoa(plan, ...)
+ * with the refinement and coefficient outputs on, then the gated inference on
+ * the [T * P] coefficient rows with the refined FCC estimate as the fallback.
+ * Requires n_in == 2K of the plan (and a head trained on the plan's grid).
+ * d_coeffs: caller workspace float [T][P][2K]; d_lag_idx, d_peak, d_tau_fcc:
+ * the plain FCC outputs [T][P]; d_tau: the gated TDoA [T][P]; d_conf may be
+ * NULL.  Two launches on `stream`, asynchronous.
+ * Errors: INVALID_ARG (sizes, pointers), UNSUPPORTED, CUDA.
+ */
+fcc_status_t fcc_tdoa_learned(fcc_plan_t *plan, fcc_mlp_t *mlp, const void *d_spectra, long long T,
+                              float threshold, int *d_lag_idx, float *d_peak, float *d_tau_fcc,
+                              float *d_coeffs, float *d_tau, float *d_conf, void *stream);
+
 /* Synchronise `stream`, then read and clear the head's device error word
  * (FCC_OK or FCC_ERR_TIMEOUT from a bounded wait of the inference kernel). */
 fcc_status_t fcc_mlp_sync(fcc_mlp_t *mlp, void *stream);

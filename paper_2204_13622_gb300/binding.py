@@ -26,7 +26,7 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc",
            # include/fcc_mlp.h
            "fcc_mlp_num_params", "fcc_mlp_create", "fcc_mlp_destroy", "fcc_mlp_get_state",
-           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer", "fcc_mlp_sync",
+           "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer", "fcc_mlp_sync", "fcc_tdoa_learned",
            # include/fcc_tune.h
            "fcc_plan_geometry", "fcc_plan_autotune",
            # include/fcc_batch.h
@@ -113,6 +113,9 @@ def lib():
         L.fcc_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp]
         L.fcc_mlp_infer.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp, _vp, _vp]
         L.fcc_mlp_sync.argtypes = [_vp, _vp]
+        L.fcc_tdoa_learned.argtypes = [_vp, _vp, _vp, ctypes.c_longlong, ctypes.c_float, _vp, _vp, _vp, _vp, _vp,
+                                       _vp, _vp]
+        L.fcc_tdoa_learned.restype = ctypes.c_int
         L.fcc_plan_geometry.argtypes = [_vp, ctypes.POINTER(Geometry)]
         L.fcc_plan_autotune.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, _dp]
         L.fcc_batch_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
@@ -280,6 +283,23 @@ class Plan:
     def sync(self, stream=None):
         """Synchronise and raise if a kernel latched an error (NaN/Inf input, timeout)."""
         check(lib().fcc_plan_sync(self._h, _stream(stream, self.device)), "fcc_plan_sync")
+
+    def tdoa_learned(self, X, mlp, threshold: float, stream=None, out=None):
+        """fcc_tdoa_learned: FCC then the learned head's gated TDoA per pair-frame."""
+        import torch
+        self._check_spectra(X)
+        T, dev = X.shape[0], X.device
+        if out is None:
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, device=dev),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, device=dev),
+                   "tau_fcc": torch.empty((T, self.P), dtype=torch.float32, device=dev),
+                   "coeffs": torch.empty((T, self.P, 2 * self.K), dtype=torch.float32, device=dev),
+                   "tau": torch.empty((T, self.P), dtype=torch.float32, device=dev),
+                   "conf": torch.empty((T, self.P), dtype=torch.float32, device=dev)}
+        check(lib().fcc_tdoa_learned(self._h, mlp._h, _ptr(X), T, float(threshold), _ptr(out["lag_idx"]),
+                                     _ptr(out["peak"]), _ptr(out["tau_fcc"]), _ptr(out["coeffs"]), _ptr(out["tau"]),
+                                     _ptr(out.get("conf")), _stream(stream, dev)), "fcc_tdoa_learned")
+        return out
 
     def geometry(self) -> dict:
         g = Geometry()

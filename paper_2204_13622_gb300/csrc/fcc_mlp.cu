@@ -720,6 +720,21 @@ fcc_status_t fcc_mlp_infer(fcc_mlp_t *h, const float *d_feat, const float *d_tau
     return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp inference");
 }
 
+fcc_status_t fcc_tdoa_learned(fcc_plan_t *plan, fcc_mlp_t *h, const void *d_spectra, long long T, float threshold,
+                              int *d_lag_idx, float *d_peak, float *d_tau_fcc, float *d_coeffs, float *d_tau,
+                              float *d_conf, void *stream)
+{
+    if (!plan || !h) return fail(FCC_ERR_INVALID_ARG, "null plan or mlp");
+    if (T < 0) return fail(FCC_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return FCC_OK;
+    if (h->nin != 2 * plan->info.K) return fail(FCC_ERR_INVALID_ARG, "the head's n_in differs from 2K of the plan");
+    if (h->device != plan->device) return fail(FCC_ERR_INVALID_ARG, "plan and head on different devices");
+    if (!d_tau_fcc || !d_coeffs || !d_tau) return fail(FCC_ERR_INVALID_ARG, "null tau_fcc / coeffs / tau");
+    fcc_status_t st = fcc_tdoa(plan, d_spectra, T, d_lag_idx, d_peak, d_tau_fcc, d_coeffs, nullptr, stream);
+    if (st != FCC_OK) return st;
+    return fcc_mlp_infer(h, d_coeffs, d_tau_fcc, T * plan->info.P, threshold, d_tau, d_conf, nullptr, stream);
+}
+
 fcc_status_t fcc_mlp_sync(fcc_mlp_t *h, void *stream)
 {
     if (!h) return fail(FCC_ERR_INVALID_ARG, "null mlp");

@@ -221,3 +221,28 @@ def test_trained_head_beats_plain_fcc(B):
     assert r["rmse_mlp_gated"] < 0.85 * r["rmse_fcc"], r
     mlp.close()
     plan.close()
+
+
+def test_tdoa_learned_chains_fcc_and_head(B):
+    """fcc_tdoa_learned = fcc_tdoa (tau_hat, coefficients) then the gated head on
+    every pair-frame's coefficients, bit for bit."""
+    from paper_2204_13622_gb300 import workloads
+    w = workloads.CIRCLE8
+    X = w.spectra(T=300, seed=5).cuda()
+    plan = B.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L)
+    K2 = 2 * plan.K
+    mlp = B.MLP(K2, synth.mlp_init_params(K2, H, seed=3), in_scale=0.5)
+    out = plan.tdoa_learned(X, mlp, threshold=0.4)
+    ref = plan.tdoa(X, tau_hat=True, coeffs=True)
+    plan.sync()
+    assert torch.equal(out["lag_idx"], ref["lag_idx"]) and torch.equal(out["peak"], ref["peak"])
+    assert torch.equal(out["tau_fcc"], ref["tau_hat"]) and torch.equal(out["coeffs"], ref["coeffs"])
+    head = mlp.infer(ref["coeffs"].view(-1, K2), ref["tau_hat"].view(-1), threshold=0.4)
+    mlp.sync()
+    assert torch.equal(out["tau"].view(-1), head["tau"]) and torch.equal(out["conf"].view(-1), head["conf"])
+    bad = B.MLP(K2 + 2, synth.mlp_init_params(K2 + 2, H, seed=3))
+    with pytest.raises(B.FccError):
+        plan.tdoa_learned(X, bad, threshold=0.4)
+    for m in (mlp, bad):
+        m.close()
+    plan.close()
