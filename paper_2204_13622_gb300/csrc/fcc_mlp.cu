@@ -280,8 +280,9 @@ __global__ void mlp_adam_kernel(float *p, const float *g, float *m, float *v, lo
 }
 
 // ---------------------------------------------------------------------------
-// Inference on the tensor cores.  One CTA of 128 threads takes 128-sample tiles
-// (thread = sample = TMEM lane).  Layer 1 and layer 2 are tcgen05.mma
+// Inference on the tensor cores.  One CTA of 256 threads takes 128-sample tiles:
+// warps w and w + 4 own TMEM lanes 32 (w % 4) .. + 31 (one sample per lane) and
+// split the 128 hidden columns in halves.  Layer 1 and layer 2 are tcgen05.mma
 // (kind::f16, BF16 x BF16 -> FP32 in TMEM, M = 128, N = 128); the activations
 // enter as a two-term BF16 split a = hi + lo (hi = bf16(a), lo = bf16(a - hi)),
 // so each layer is two MMA passes against the same BF16 weights and the
@@ -289,10 +290,11 @@ __global__ void mlp_adam_kernel(float *p, const float *g, float *m, float *v, lo
 // training kernels.  The epilogues read TMEM with tcgen05.ld (bias, exact-erf
 // GELU, the split for the next layer; layer 3 and the gate on the CUDA cores).
 constexpr int kTcRows = 128;
+constexpr int kTcThreads = 256;
 
 struct TcMlpLayout {
     int K1;  // layer-1 K: n_in padded to a multiple of 16
-    size_t w1, w2, abuf, w3, b1, b2, total;
+    size_t w1, w2, abuf, w3, b1, b2, part, total;
 };
 
 __host__ __device__ inline TcMlpLayout tc_mlp_layout(int nin)
@@ -311,7 +313,9 @@ __host__ __device__ inline TcMlpLayout tc_mlp_layout(int nin)
     L.b1 = o;
     o += kH * 4;
     L.b2 = o;
-    o += kH * 4 + 16;
+    o += kH * 4;
+    L.part = o;
+    o += (size_t)kTcRows * 2 * 4 + 16;  // layer-3 partial sums of the second column half
     L.total = o;
     return L;
 }
@@ -341,9 +345,9 @@ __device__ __forceinline__ void store_split8(unsigned char *A, int r, int k, int
         make_uint4(bf2(lo[0], lo[1]), bf2(lo[2], lo[3]), bf2(lo[4], lo[5]), bf2(lo[6], lo[7]));
 }
 
-__global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const float *feat, const float *tau_fcc,
-                                                               long long n, float threshold, float *tau_out,
-                                                               float *conf_out, float *raw_out, unsigned *err)
+__global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(MlpW w, const float *feat, const float *tau_fcc,
+                                                                  long long n, float threshold, float *tau_out,
+                                                                  float *conf_out, float *raw_out, unsigned *err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int nin = w.nin;
@@ -354,25 +358,26 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const flo
     int *abort_flag = reinterpret_cast<int *>(smem + 12);
     unsigned char *W1s = smem + L.w1, *W2s = smem + L.w2, *A = smem + L.abuf;
     float *W3s = reinterpret_cast<float *>(smem + L.w3), *b1s = reinterpret_cast<float *>(smem + L.b1),
-          *b2s = reinterpret_cast<float *>(smem + L.b2);
-    const int r = threadIdx.x, warp = r >> 5;
+          *b2s = reinterpret_cast<float *>(smem + L.b2), *part = reinterpret_cast<float *>(smem + L.part);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = (warp & 3) * 32 + (tid & 31);  // sample row = TMEM lane
+    const int half = warp >> 2;                  // hidden columns [64 half, 64 half + 64)
 
     // weights into shared memory, once per CTA
-    for (int e = r; e < kH * K1; e += blockDim.x) {
+    for (int e = tid; e < kH * K1; e += blockDim.x) {
         const int o = e / K1, k = e % K1;
         *reinterpret_cast<__nv_bfloat16 *>(W1s + kmaj(o, k, K1)) =
             k < nin ? w.W1[o * nin + k] : __float2bfloat16_rn(0.f);
     }
-    for (int e = r; e < kH * kH; e += blockDim.x)
+    for (int e = tid; e < kH * kH; e += blockDim.x)
         *reinterpret_cast<__nv_bfloat16 *>(W2s + kmaj(e / kH, e % kH, kH)) = w.W2[e];
-    for (int e = r; e < 2 * kH; e += blockDim.x) W3s[e] = __bfloat162float(w.W3[e]);
-    b1s[r] = w.b1[r];
-    b2s[r] = w.b2[r];
+    for (int e = tid; e < 2 * kH; e += blockDim.x) W3s[e] = __bfloat162float(w.W3[e]);
+    for (int e = tid; e < kH; e += blockDim.x) {
+        b1s[e] = w.b1[e];
+        b2s[e] = w.b2[e];
+    }
     const float b30 = w.b3[0], b31 = w.b3[1];
-    float sc[kMaxIn];
-#pragma unroll
-    for (int k = 0; k < kMaxIn; ++k) sc[k] = k < nin ? w.scale[k] : 0.f;
-    if (r == 0) {
+    if (tid == 0) {
         mbar_init(bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const flo
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t t_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(64 * half);
     // instruction descriptor: D FP32, A and B BF16, K-major, N = 128, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
     const uint32_t a_addr = smem_u32(A), w1_addr = smem_u32(W1s), w2_addr = smem_u32(W2s);
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const flo
         fence_proxy_async();  // our generic stores of A -> the tensor cores' reads
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (r == 0) {
+        if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (layer == 1) {
                 const uint32_t sbo_a = (uint32_t)(2 * K1 / 8) * 128, sbo_b = (uint32_t)(K1 / 8) * 128;
@@ -425,57 +430,67 @@ __global__ void __launch_bounds__(kTcRows) mlp_infer_tc_kernel(MlpW w, const flo
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const long long s = t * kTcRows + r;
         const bool live = s < n;
-        // ---- A of layer 1: scaled features, split into hi | lo
-        {
-            float x[kMaxIn];
+        // ---- A of layer 1: scaled features split into hi | lo; the two halves
+        // of the CTA take alternate groups of 8 features
+        for (int k = 8 * half; k < K1; k += 16) {
+            float x[8];
 #pragma unroll
-            for (int k = 0; k < kMaxIn; ++k) x[k] = (live && k < nin) ? feat[(size_t)s * nin + k] * sc[k] : 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxIn; k += 8)
-                if (k < K1) store_split8(A, r, k, 2 * K1, K1, x + k);
+            for (int j = 0; j < 8; ++j)
+                x[j] = (live && k + j < nin) ? feat[(size_t)s * nin + k + j] * w.scale[k + j] : 0.f;
+            store_split8(A, r, k, 2 * K1, K1, x);
         }
         if (!mma_and_wait(1)) {
             failed = true;
             break;
         }
         // ---- epilogue 1: bias, GELU, split into the A of layer 2
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+            const int c = 64 * half + c0;
             float v[32];
             tmem_ld32(t_row + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1s[c0 + j]);
+            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1s[c + j]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) store_split8(A, r, c0 + j, 2 * kH, kH, v + j);
+            for (int j = 0; j < 32; j += 8) store_split8(A, r, c + j, 2 * kH, kH, v + j);
         }
         if (!mma_and_wait(2)) {
             failed = true;
             break;
         }
-        // ---- epilogue 2: bias, GELU, layer 3, gate
-        float y0 = b30, y1 = b31;
-        for (int c0 = 0; c0 < kH; c0 += 32) {
+        // ---- epilogue 2: bias, GELU, layer 3 over this half's columns
+        float y0 = 0.f, y1 = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+            const int c = 64 * half + c0;
             float v[32];
             tmem_ld32(t_row + c0, v);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const float h = gelu(v[j] + b2s[c0 + j]);
-                y0 = fmaf(W3s[c0 + j], h, y0);
-                y1 = fmaf(W3s[kH + c0 + j], h, y1);
+                const float h = gelu(v[j] + b2s[c + j]);
+                y0 = fmaf(W3s[c + j], h, y0);
+                y1 = fmaf(W3s[kH + c + j], h, y1);
             }
         }
-        if (live) {
+        if (half == 1) {
+            part[2 * r] = y0;
+            part[2 * r + 1] = y1;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // partials visible; TMEM and A are free for the next tile
+        if (half == 0 && live) {
+            y0 = b30 + (y0 + part[2 * r]);
+            y1 = b31 + (y1 + part[2 * r + 1]);
             const float c = 1.f / (1.f + expf(-y1));
             tau_out[s] = (c >= threshold || !tau_fcc) ? y0 : tau_fcc[s];
             if (conf_out) conf_out[s] = c;
             if (raw_out) raw_out[s] = y0;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // TMEM and A are free for the next tile
     }
     if (failed) {
-        if (r == 0) atomicOr(err, kErrTimeout);
+        if (tid == 0) atomicOr(err, kErrTimeout);
         // the last MMAs may still be running: wait once more (bounded) before freeing TMEM
-        if (!mbar_wait(bar, phase ^ 1u) && r == 0) atomicOr(err, kErrTimeout);
+        if (!mbar_wait(bar, phase ^ 1u) && tid == 0) atomicOr(err, kErrTimeout);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -714,7 +729,7 @@ fcc_status_t fcc_mlp_infer(fcc_mlp_t *h, const float *d_feat, const float *d_tau
     }
     const long long tiles = (n + kTcRows - 1) / kTcRows;
     const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * 2);
-    mlp_infer_tc_kernel<<<grid, kTcRows, smem, static_cast<cudaStream_t>(stream)>>>(
+    mlp_infer_tc_kernel<<<grid, kTcThreads, smem, static_cast<cudaStream_t>(stream)>>>(
         weights(h), d_feat, d_tau_fcc, n, threshold, d_tau, d_conf, d_raw, h->d_err);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FCC_OK : cuda_fail(e, "mlp inference");
