@@ -265,12 +265,27 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                     bE[v] = pk(w[v], w[v]);
                     bO[v] = pk(w[KH + v], w[KH + v]);
                 }
+                // packed operands: x as (re, im) and swapped (im, re) per X microphone
+                // and bin, y as (re, re) and (im, -im) per Y microphone and bin, so
+                // that x y^* = (xr yr + xi yi, xi yr - xr yi) is one FMUL2 + one FFMA2
+                f2 xa[2][2], xw[2][2], yr[2][2], yi[2][2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    xa[u][0] = pk(X[u].x, X[u].y);
+                    xw[u][0] = pk(X[u].y, X[u].x);
+                    xa[u][1] = pk(X[u].z, X[u].w);
+                    xw[u][1] = pk(X[u].w, X[u].z);
+                    yr[u][0] = pk(Y[u].x, Y[u].x);
+                    yi[u][0] = pk(Y[u].y, -Y[u].y);
+                    yr[u][1] = pk(Y[u].z, Y[u].z);
+                    yi[u][1] = pk(Y[u].w, -Y[u].w);
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float4 x = X[q >> 1], y = Y[q & 1];
+                    const int ix = q >> 1, iy = q & 1;
                     // cross spectra at f and N/2 - f: a = x(f) y(f)^*, b = x(N/2-f) y(N/2-f)^*
-                    const f2 a = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
-                    const f2 b = pk(fmaf(x.z, y.z, x.w * y.w), fmaf(x.w, y.z, -(x.z * y.w)));
+                    const f2 a = fma2(xw[ix][0], yi[iy][0], mul2(xa[ix][0], yr[iy][0]));
+                    const f2 b = fma2(xw[ix][1], yi[iy][1], mul2(xa[ix][1], yr[iy][1]));
                     const f2 xs = add2(a, b), xd = sub2(a, b);  // Eq. 8
 #pragma unroll
                     for (int v = 0; v < KH; ++v) {
@@ -281,11 +296,18 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             };
             const int cb = chunk * QC;
             const int st_off = (int)(st - smem);
+            // Each lane takes its slot's microphones in the order of its role in
+            // the reduce-scatter: chunk bit 1 swaps the two X microphones, chunk
+            // bit 0 the two Y microphones, so accumulator q always holds the pair
+            // this lane keeps (q = 0) or hands on, with no selects.
+            const int sx = (chunk >> 1) & 1, sy = chunk & 1;
+            const int mr[4] = {sx ? sl.mic[1] : sl.mic[0], sx ? sl.mic[0] : sl.mic[1],
+                               sy ? sl.mic[3] : sl.mic[2], sy ? sl.mic[2] : sl.mic[3]};
             int sw[4], rb[4];  // byte offsets from the shared-memory base
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                sw[r] = rec_swz(R0 + sl.mic[r], Q);
-                rb[r] = st_off + rec_off(R0 + sl.mic[r], B) + 16 * cb;
+                sw[r] = rec_swz(R0 + mr[r], Q);
+                rb[r] = st_off + rec_off(R0 + mr[r], B) + 16 * cb;
             }
             if ((QC & 7) == 0) {
                 // 8 records at a time: record cb+t8+j of a swizzled row is at
@@ -376,29 +398,29 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
         // ---- 4. reduce-scatter of the chunk partials: lane (chunk & 3) keeps pair (chunk & 3)
         f2 zE[KH], zO[KH];
         {
-            const bool hi = (chunk & 2) != 0;
+            // level 1 (lanes 2 SB apart): keep accumulators 0, 1, hand on 2, 3
             f2 rE[2][KH], rO[2][KH];
 #pragma unroll
             for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
                 for (int v = 0; v < KH; ++v) {
                     float m0, m1, o0, o1;
-                    upk(hi ? accE[pp + 2][v] : accE[pp][v], m0, m1);
-                    upk(hi ? accE[pp][v] : accE[pp + 2][v], o0, o1);
+                    upk(accE[pp][v], m0, m1);
+                    upk(accE[pp + 2][v], o0, o1);
                     rE[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
-                    upk(hi ? accO[pp + 2][v] : accO[pp][v], m0, m1);
-                    upk(hi ? accO[pp][v] : accO[pp + 2][v], o0, o1);
+                    upk(accO[pp][v], m0, m1);
+                    upk(accO[pp + 2][v], o0, o1);
                     rO[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
                 }
-            const bool b0 = (chunk & 1) != 0;
+            // level 2 (lanes SB apart): keep 0, hand on 1; then plain sums over the other chunks
 #pragma unroll
             for (int v = 0; v < KH; ++v) {
                 float m0, m1, o0, o1;
-                upk(b0 ? rE[1][v] : rE[0][v], m0, m1);
-                upk(b0 ? rE[0][v] : rE[1][v], o0, o1);
+                upk(rE[0][v], m0, m1);
+                upk(rE[1][v], o0, o1);
                 float e0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), e1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
-                upk(b0 ? rO[1][v] : rO[0][v], m0, m1);
-                upk(b0 ? rO[0][v] : rO[1][v], o0, o1);
+                upk(rO[0][v], m0, m1);
+                upk(rO[1][v], o0, o1);
                 float d0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), d1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
                 for (int o = 4 * p.SB; o < 32; o <<= 1) {
                     e0 += __shfl_xor_sync(FULLM, e0, o);
