@@ -111,7 +111,9 @@ __device__ __forceinline__ float2 unit_phase_fast(float2 x, bool &ok)
     const float s = fmaf(x.x, x.x, x.y * x.y);
     ok = (s >= FLT_MIN) && (s <= FLT_MAX);
     const float r = rsqrtf(s);
-    return make_float2(x.x * r, x.y * r);
+    float a, b;
+    upk(mul2(pk(x.x, x.y), pk(r, r)), a, b);
+    return make_float2(a, b);
 }
 // u = x / |x| with u = 0 for x = 0; rescaled for |x|^2 outside the normal FP32
 // range; flags NaN / Inf (u = 0).
