@@ -256,6 +256,8 @@ def run_fcc(args, rank, world, local):
 
     # ---- roofline of the dominant (only) kernel: algorithmic bytes per launch
     bytes_per_launch = T * (w.M * w.B * 8) + T * P * 12  # spectra read + idx/peak/tau_hat written
+    # and its CUDA-core arithmetic: FP32 operations per pair-frame (FMA = 1)
+    ops_pf = fp32_ops_per_pair_frame(w.M, w.N, plan.K_even, plan.K_odd, plan.I)
     acc = accuracy_vs_oracle(w, plan, X, out) if rank == 0 else None
     achieved = bytes_per_launch / (ms / 1000.0) / 1e9
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -341,6 +343,7 @@ def run_fcc(args, rank, world, local):
                          "kernel": "fcc_fp32_kernel" if args.prec == "fp32" else "fcc_tc_kernel",
                          "bytes_per_launch": bytes_per_launch,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+            "roofline_alu": alu_roofline(ops_pf * T * P, ms, "fcc_fp32_kernel") if args.prec == "fp32" else None,
             "gcc_phat": {"value": world * T * P / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms,
                          "r": w.lag_den, "argmax_agreement_with_fcc": agree},
             "fcc_vs_gcc": (gms / ms),
@@ -353,6 +356,31 @@ def run_fcc(args, rank, world, local):
         }
     plan.close()
     return res
+
+
+# FP32 pipe of one GB300: 152 SMs x 128 FP32 lanes x 2070 MHz (maximum SM clock),
+# one FMA (or add, or multiply) per lane per clock
+FP32_PEAK_OPS = 152 * 128 * 2.070e9
+
+
+def fp32_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float:
+    """FP32 operations per pair-frame of the FP32 kernel's arithmetic (FMA = 1):
+    the cross spectrum (4 per bin), the Eq. 8 fold (4 per bin pair), the even and
+    odd projections (2 per basis and bin), the reconstruction over tau >= 0 (4K + 2
+    per lag step, both signs at once) and this pair's share of the per-microphone
+    PHAT (5 per microphone bin)."""
+    B, Q = N // 2 + 1, N // 4
+    P = M * (M - 1) // 2
+    center = (I - 1) // 2
+    return (4 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (4 * (KE + KO) + 2)
+            + 5.0 * M * B / P)
+
+
+def alu_roofline(ops: float, ms: float, kernel: str) -> dict:
+    achieved = ops / (ms / 1000.0)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_OPS / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_OPS, "kernel": kernel, "ops_per_launch": ops,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FMA counted once)"}
 
 
 def _peak_hbm():
@@ -407,6 +435,8 @@ def run_batched(args, rank, world, local):
     value = whole_job_rate(info["pair_frames"], world, ms_max / 1000.0)
     bytes_per_step = info["spectra_bytes"] + info["result_bytes"]
     achieved = bytes_per_step / (ms / 1000.0) / 1e9
+    ops = sum(fp32_ops_per_pair_frame(a["M"], a["N"], a["K_even"], a["K_odd"], a["I"]) * t * a["P"]
+              for a, t in zip(batch.arrays, batch.T))
     peak, psrc = _peak_hbm()
     res = None
     if rank == 0:
@@ -436,6 +466,7 @@ def run_batched(args, rank, world, local):
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": None, "kernel": "fcc_fp32_batch_kernel",
                             "bytes_per_launch": bytes_per_step, "peak_source": psrc},
+               "roofline_alu": alu_roofline(ops, ms, "fcc_fp32_batch_kernel"),
                "accuracy_vs_oracle": {"pair_frames": int(n_pf), "argmax_agreement": float(agree.mean())},
                "cpu_baseline": {"value": n_pf / t_or, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
                                 "sample": f"16 frames of 8 arrays ({n_pf} pair-frames), FP64 C oracle"},
