@@ -118,3 +118,62 @@ def pick_threshold(mlp, data, grid=THRESHOLDS) -> float:
     t, raw, fcc, conf = data["t"], out["raw"], data["tau_fcc"], out["conf"]
     best = min(grid, key=lambda th: rmse(torch.where(conf >= th, raw, fcc), t))
     return float(best)
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / resume: a flat little-endian file
+#   magic "FCCMLP01", header length (u32), JSON header (n_in, hidden, step,
+#   threshold, conf_weight, basis_sha256 of the plan the head was trained on),
+#   then float32 in_scale[n_in], params[n], adam_m[n], adam_v[n]
+# ---------------------------------------------------------------------------
+MAGIC = b"FCCMLP01"
+
+
+def basis_hash(plan) -> str:
+    """SHA-256 of the plan's FP64 bases and lag grid: a head is only valid for the
+    coefficients of the bases it was trained on."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in plan.bases() + (plan.taus(),):
+        h.update(np.ascontiguousarray(a, np.float64).tobytes())
+    return h.hexdigest()
+
+
+def save(path: str, mlp, plan, scale, threshold: float, conf_weight: float = 0.1) -> None:
+    import json
+    import struct
+    p, m, v, step = mlp.get_state()
+    scale = np.ascontiguousarray(scale, np.float32).reshape(mlp.n_in)
+    hdr = json.dumps({"n_in": mlp.n_in, "hidden": HIDDEN, "n_params": int(p.size), "step": int(step),
+                      "threshold": float(threshold), "conf_weight": float(conf_weight),
+                      "basis_sha256": basis_hash(plan)}).encode()
+    with open(path, "wb") as f:
+        f.write(MAGIC)
+        f.write(struct.pack("<I", len(hdr)))
+        f.write(hdr)
+        for a in (scale, p, m, v):
+            f.write(np.ascontiguousarray(a, "<f4").tobytes())
+
+
+def load(path: str, plan, device: int | None = None):
+    """Returns (mlp, threshold).  Raises if the file is not a head checkpoint or
+    was trained on other bases than `plan`'s."""
+    import json
+    import struct
+    with open(path, "rb") as f:
+        if f.read(8) != MAGIC:
+            raise ValueError(f"{path}: not a learned-head checkpoint")
+        (n,) = struct.unpack("<I", f.read(4))
+        hdr = json.loads(f.read(n).decode())
+        if hdr["basis_sha256"] != basis_hash(plan):
+            raise ValueError(f"{path}: trained on other bases than this plan's")
+        if hdr["n_in"] != 2 * plan.K or hdr["hidden"] != HIDDEN:
+            raise ValueError(f"{path}: shape does not match the plan")
+        k, npar = hdr["n_in"], hdr["n_params"]
+        body = np.frombuffer(f.read(4 * (k + 3 * npar)), "<f4")
+    if body.size != k + 3 * npar:
+        raise ValueError(f"{path}: truncated")
+    scale, p, m, v = body[:k], body[k:k + npar], body[k + npar:k + 2 * npar], body[k + 2 * npar:]
+    mlp = binding.MLP(k, p, in_scale=scale, conf_weight=hdr["conf_weight"], device=device)
+    mlp.set_state(p, m, v, step=hdr["step"])
+    return mlp, hdr["threshold"]

@@ -164,3 +164,36 @@ def test_batch_autotune_flag(B, tmp_path):
     batch.run()
     batch.sync()
     batch.close()
+
+
+def test_batch_rebind_to_new_buffers(B):
+    arrs = _small_arrays(10, seed=11)
+    batch = B.Batch(arrs)
+    X1 = [synth.array_spectra(a, device="cuda") for a in arrs]
+    X2 = [synth.array_spectra(dict(a, seed=a["seed"] + 1), device="cuda") for a in arrs]
+    o1, o2 = batch.outputs(), batch.outputs()
+    batch.bind(X1, o1)
+    batch.run()
+    batch.sync()
+    batch.bind(X2, o2)  # the same graph reads the new parameter table
+    batch.run()
+    batch.sync()
+    for a, arr in enumerate(arrs):
+        plan = B.Plan(**_plan_kw(arr))
+        r1, r2 = plan.tdoa(X1[a]), plan.tdoa(X2[a])
+        plan.sync()
+        for k in ("lag_idx", "peak", "tau_hat"):
+            assert torch.equal(r1[k], o1[a][k]) and torch.equal(r2[k], o2[a][k]), (a, k)
+        plan.close()
+    batch.close()
+
+
+def test_autotune_ignores_a_corrupt_cache(B, tmp_path):
+    cache = tmp_path / "tune.json"
+    cache.write_text("{ this is not json")
+    plan = B.Plan(4, 16000.0, 512, 4, tau_max=3)
+    us = plan.autotune(str(cache), max_candidates=2)
+    assert us > 0
+    data = json.load(open(cache))  # rewritten as a valid cache
+    assert len(data["entries"]) == 1
+    plan.close()

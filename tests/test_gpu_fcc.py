@@ -218,6 +218,21 @@ def test_host_entry_point_matches_device(B):
     plan.close()
 
 
+def test_host_entry_point_odd_mics_and_chunking(B):
+    # 3 microphones: a frame (6168 B) is not a multiple of 16 bytes, so the
+    # kernel stages with plain loads; 40001 frames leave a ragged last tile
+    rng = np.random.default_rng(8)
+    T = 40001
+    X = (rng.standard_normal((T, 3, 257)) + 1j * rng.standard_normal((T, 3, 257))).astype(np.complex64)
+    plan = B.Plan(3, 16000.0, 512, 4, tau_max=3)
+    dev = plan.tdoa(torch.from_numpy(X).cuda())
+    plan.sync()
+    host = plan.tdoa_host(torch.from_numpy(X).pin_memory())
+    for k in ("lag_idx", "peak", "tau_hat"):
+        assert torch.equal(dev[k].cpu(), host[k]), k
+    plan.close()
+
+
 # --------------------------------------------------------------------------
 # GCC-PHAT baseline (full rank, cuFFT) against eq. 2 in the oracle
 # --------------------------------------------------------------------------

@@ -246,3 +246,29 @@ def test_tdoa_learned_chains_fcc_and_head(B):
     for m in (mlp, bad):
         m.close()
     plan.close()
+
+
+def test_checkpoint_file_roundtrip_and_basis_binding(B, tmp_path):
+    from paper_2204_13622_gb300 import learned
+    plan = learned.pair_plan()
+    K2 = 2 * plan.K
+    scale = np.linspace(0.5, 2.0, K2).astype(np.float32)
+    mlp = learned.new_head(K2, scale, seed=4)
+    rng = np.random.default_rng(0)
+    f_d = torch.from_numpy(rng.standard_normal((4096, K2)).astype(np.float32)).cuda()
+    t_d = torch.from_numpy(rng.uniform(-4, 4, 4096).astype(np.float32)).cuda()
+    mlp.train_step(f_d, t_d, t_d + 0.1, 1e-3)
+    path = str(tmp_path / "head.bin")
+    learned.save(path, mlp, plan, scale, threshold=0.35)
+    back, th = learned.load(path, plan)
+    assert th == 0.35
+    for u, v in zip(mlp.get_state(), back.get_state()):
+        assert np.array_equal(u, v)
+    a = mlp.infer(f_d, t_d, 0.35)
+    b = back.infer(f_d, t_d, 0.35)
+    assert torch.equal(a["tau"], b["tau"]) and torch.equal(a["conf"], b["conf"])  # same scale, same weights
+    other = B.Plan(2, 16000.0, 512, 8, tau_max=4.66)  # another lag grid: other bases
+    with pytest.raises(ValueError):
+        learned.load(path, other)
+    for o in (mlp, back, other, plan):
+        o.close()
