@@ -436,30 +436,9 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
         // ---- 5. reconstruction on the grid, argmax, peak, refinement
         const int q = chunk & 3;
         const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
-        if (active && chunk < 4 && pq >= 0) {
-            const size_t o = (size_t)(f0 + fl) * p.P + pq;
-            float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
-            float S, D;
-            eval_SD<KH>(recon, 0, zE, zO, S, D);
-            float best = S - D;
-            int bi = p.center;
-            if (corr) corr[p.center] = best;
-            for (int m = 1; m <= p.center; ++m) {
-                eval_SD<KH>(recon, m, zE, zO, S, D);
-                const float ym = S + D, yp = S - D;  // y(center - m), y(center + m)
-                if (ym >= best) {  // lower index than everything seen so far
-                    best = ym;
-                    bi = p.center - m;
-                }
-                if (yp > best) {  // higher index than everything seen so far
-                    best = yp;
-                    bi = p.center + m;
-                }
-                if (corr) {
-                    corr[p.center - m] = ym;
-                    corr[p.center + m] = yp;
-                }
-            }
+        // The pair's y(tau) values at bi - 1 and bi + 1 (FP64 differences) give the
+        // three-point parabola; the coefficients go out when asked for.
+        auto emit = [&](size_t o, int bi, float best) {
             p.out_idx[o] = bi;
             p.out_peak[o] = best;
             if (p.out_tau) {
@@ -493,6 +472,74 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                     }
                 }
             }
+        };
+        // One outward scan over lag steps m = m0, m0 + stride, ...: y(center - m)
+        // is below every index this lane has seen (wins ties), y(center + m)
+        // above every one (loses ties).
+        auto scan = [&](int m0, int stride, float &best, int &bi, float *corr) {
+            float S, D;
+            for (int m = m0; m <= p.center; m += stride) {
+                eval_SD<KH>(recon, m, zE, zO, S, D);
+                const float ym = S + D, yp = S - D;  // y(center - m), y(center + m)
+                if (ym >= best) {
+                    best = ym;
+                    bi = p.center - m;
+                }
+                if (yp > best) {
+                    best = yp;
+                    bi = p.center + m;
+                }
+                if (corr) {
+                    corr[p.center - m] = ym;
+                    corr[p.center + m] = yp;
+                }
+            }
+        };
+        if (p.C == 4) {
+            // one chunk lane per pair
+            if (active && pq >= 0) {
+                const size_t o = (size_t)(f0 + fl) * p.P + pq;
+                float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
+                float S, D;
+                eval_SD<KH>(recon, 0, zE, zO, S, D);
+                float best = S - D;
+                int bi = p.center;
+                if (corr) corr[p.center] = best;
+                scan(1, 1, best, bi, corr);
+                emit(o, bi, best);
+            }
+        } else {
+            // the C / 4 chunk lanes holding the same pair (the reduction leaves
+            // its coefficients in all of them) split the lag steps m = gi,
+            // gi + C/4, ... and combine their maxima with shuffles: value first,
+            // then the lower lag index, as one outward scan would
+            const int G4 = p.C >> 2, gi = chunk >> 2;
+            const bool mine = active && pq >= 0;
+            const size_t o = mine ? (size_t)(f0 + fl) * p.P + pq : 0;
+            float best = -FLT_MAX;
+            int bi = 0x7fffffff;
+            if (mine) {
+                float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
+                int m0 = gi;
+                if (gi == 0) {
+                    float S, D;
+                    eval_SD<KH>(recon, 0, zE, zO, S, D);
+                    best = S - D;
+                    bi = p.center;
+                    if (corr) corr[p.center] = best;
+                    m0 = G4;
+                }
+                scan(m0, G4, best, bi, corr);
+            }
+            for (int off = 4 * p.SB; off < 32; off <<= 1) {
+                const float ob = __shfl_xor_sync(FULLM, best, off);
+                const int oi = __shfl_xor_sync(FULLM, bi, off);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (mine && gi == 0) emit(o, bi, best);
         }
     }
     // never retire with one of this group's bulk copies still in flight
