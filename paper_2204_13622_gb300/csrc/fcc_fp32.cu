@@ -318,7 +318,10 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                     lo[r] = rb[r] + 16 * sw[r];
                     hi[r] = rb[r] - 16 * sw[r];
                 }
-#pragma unroll 1
+                // two 8-record blocks per iteration pay for KH = 8 (16-mic grid: 8 %
+                // faster) and cost the 4-basis kernels (8-mic circle: 11 % slower)
+                constexpr int kBlockUnroll = KH >= 8 ? 2 : 1;
+#pragma unroll kBlockUnroll
                 for (int t8 = 0; t8 < QC; t8 += 8) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
