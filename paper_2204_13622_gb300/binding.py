@@ -31,7 +31,9 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            "fcc_plan_geometry", "fcc_plan_autotune",
            # include/fcc_batch.h
            "fcc_batch_create", "fcc_batch_destroy", "fcc_batch_info", "fcc_batch_array_info", "fcc_batch_bind",
-           "fcc_batch_run", "fcc_batch_sync"]
+           "fcc_batch_run", "fcc_batch_sync",
+           # include/fcc_debug.h
+           "fcc_debug_set"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -62,6 +64,12 @@ class BatchInfo(ctypes.Structure):
 
 
 FCC_BATCH_AUTOTUNE = 1
+DEBUG_HOOKS = {"wait_cycles": 0, "withhold_copy": 1, "fail_alloc": 2}
+
+
+def debug_set(hook: str, value: int):
+    """Test hooks of include/fcc_debug.h (wait bound, withheld copies, failing allocations)."""
+    check(lib().fcc_debug_set(DEBUG_HOOKS[hook], int(value)), "fcc_debug_set")
 
 
 class FccError(RuntimeError):
@@ -127,6 +135,8 @@ def lib():
         L.fcc_batch_bind.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                      ctypes.POINTER(_vp)]
         L.fcc_batch_run.argtypes = [_vp, _vp]
+        L.fcc_debug_set.argtypes = [ctypes.c_int, ctypes.c_longlong]
+        L.fcc_debug_set.restype = ctypes.c_int
         L.fcc_batch_sync.argtypes = [_vp, _vp]
         for name in ("fcc_plan_geometry", "fcc_plan_autotune", "fcc_batch_create", "fcc_batch_info",
                      "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):

@@ -7,6 +7,7 @@
 #include <new>
 #include <string>
 
+#include "fcc_debug.h"
 #include "fcc_internal.h"
 
 namespace fcc {
@@ -23,6 +24,23 @@ fcc_status_t cuda_fail(cudaError_t e, const char *what)
 {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? FCC_ERR_OOM : FCC_ERR_CUDA;
+}
+
+DebugHooks &debug_hooks()
+{
+    static DebugHooks h{2000000000LL, 0, 0};
+    return h;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    DebugHooks &h = debug_hooks();
+    if (h.fail_allocs > 0) {
+        --h.fail_allocs;
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 namespace {
@@ -118,8 +136,8 @@ fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g)
     if (g.C) pack_tables(plan, basis, recon);
     else basis.assign(4, 0.f), recon.assign(4, 0.f);  // N > 1024: no FP32 kernel
     float *nb = nullptr, *nr = nullptr;
-    cudaError_t e = cudaMalloc(&nb, basis.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&nr, recon.size() * sizeof(float));
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&nb), basis.size() * sizeof(float));
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&nr), recon.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(nb, basis.data(), basis.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(nr, recon.data(), recon.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -237,6 +255,26 @@ const char *fcc_status_string(fcc_status_t s)
 
 const char *fcc_last_error(void) { return g_last_error.c_str(); }
 
+fcc_status_t fcc_debug_set(int hook, long long value)
+{
+    DebugHooks &h = debug_hooks();
+    switch (hook) {
+    case FCC_DEBUG_WAIT_CYCLES:
+        if (value != 0 && value < 1000) return fail(FCC_ERR_INVALID_ARG, "wait bound below 1000 cycles");
+        h.wait_cycles = value ? value : 2000000000LL;
+        return FCC_OK;
+    case FCC_DEBUG_WITHHOLD_COPY:
+        if (value < 0 || value > (1 << 30)) return fail(FCC_ERR_INVALID_ARG, "count out of range");
+        h.withhold_copies = (int)value;
+        return FCC_OK;
+    case FCC_DEBUG_FAIL_ALLOC:
+        if (value < 0 || value > (1 << 30)) return fail(FCC_ERR_INVALID_ARG, "count out of range");
+        h.fail_allocs = (int)value;
+        return FCC_OK;
+    }
+    return fail(FCC_ERR_INVALID_ARG, "unknown debug hook");
+}
+
 fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
 {
     g_last_error.clear();
@@ -277,9 +315,9 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
             return st;
         }
     }
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_slots, slots.size() * sizeof(Slot));
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&p->d_slots), slots.size() * sizeof(Slot));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_slots, slots.data(), slots.size() * sizeof(Slot), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&p->d_err), sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
         free_plan(p);

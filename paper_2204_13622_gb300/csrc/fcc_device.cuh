@@ -84,13 +84,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 // Bounded wait on an mbarrier phase; false if it did not complete in time.
-__device__ bool mbar_wait(uint64_t *bar, unsigned parity)
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
         __nanosleep(64);
     }
 }

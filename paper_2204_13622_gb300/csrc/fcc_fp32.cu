@@ -141,11 +141,13 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                  reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes, bytes, &full[s]);
     };
 
-    // prime this group's stages
+    // prime this group's stages (the test hook withholds CTA 0's first copy, so
+    // that group's first wait runs out and the timeout path is taken)
     const int Sg = p.S / p.G;
     if (p.bulk && leader)
         for (int j = 0; j < Sg; ++j)
-            if (group + j * p.G < n_local) issue(group + j * p.G);
+            if (group + j * p.G < n_local && !(p.inject && blockIdx.x == 0 && group == 0 && j == 0))
+                issue(group + j * p.G);
 
     // lane -> (frame in tile, slot, chunk).  A frame takes n_blocks whole warps;
     // inside a warp the lanes are chunk-major (lane = chunk * SB + slot), so the
@@ -175,7 +177,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             for (size_t e = lane_g; e < n8; e += p.GW * 32) dst[e] = __ldg(src + e);
             mbar_arrive(&full[s]);
         }
-        if (!mbar_wait(&full[s], par)) {
+        if (!mbar_wait(&full[s], par, p.wait_cycles)) {
             if (lane == 0) atomicOr(p.err, kErrTimeout);
             break;
         }
@@ -229,7 +231,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
         }
         if (p.GW > 1) {
             if (lane == 0) mbar_arrive(&normd[s]);
-            if (!mbar_wait(&normd[s], par)) {
+            if (!mbar_wait(&normd[s], par, p.wait_cycles)) {
                 if (lane == 0) atomicOr(p.err, kErrTimeout);
                 break;
             }
@@ -378,7 +380,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             if (p.GW > 1) {
                 if (lane == 0) mbar_arrive(&freed[s]);
                 if (leader && k + p.S < n_local) {
-                    if (!mbar_wait(&freed[s], par)) {
+                    if (!mbar_wait(&freed[s], par, p.wait_cycles)) {
                         atomicOr(p.err, kErrTimeout);
                     } else {
                         issue(k + p.S);
@@ -391,7 +393,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             // plain staging: the group's next copy must not start before every
             // warp has left this stage
             if (lane == 0) mbar_arrive(&freed[s]);
-            if (!mbar_wait(&freed[s], par)) {
+            if (!mbar_wait(&freed[s], par, p.wait_cycles)) {
                 if (lane == 0) atomicOr(p.err, kErrTimeout);
                 break;
             }
@@ -548,7 +550,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
     // never retire with one of this group's bulk copies still in flight
     if (p.bulk && leader) {
         for (int k = k_done + p.G; k < n_local && k <= k_done + p.S; k += p.G)
-            if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u)) atomicOr(p.err, kErrTimeout);
+            if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u, p.wait_cycles)) atomicOr(p.err, kErrTimeout);
     }
 }
 
@@ -738,6 +740,13 @@ Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long lo
     prm.out_coef = coef;
     prm.out_corr = corr;
     prm.err = err;
+    DebugHooks &dh = debug_hooks();
+    prm.wait_cycles = dh.wait_cycles;
+    prm.inject = 0;
+    if (dh.withhold_copies > 0) {
+        --dh.withhold_copies;
+        prm.inject = 1;
+    }
     return prm;
 }
 

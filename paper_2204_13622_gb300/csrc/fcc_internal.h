@@ -21,6 +21,16 @@ enum : unsigned {
 fcc_status_t fail(fcc_status_t st, const std::string &msg);
 fcc_status_t cuda_fail(cudaError_t e, const char *what);
 
+// Test hooks (include/fcc_debug.h), process-wide.
+struct DebugHooks {
+    long long wait_cycles;  // device wait bound for FP32 launches
+    int withhold_copies;    // FP32 launches left that withhold one bulk copy
+    int fail_allocs;        // plan allocations left that fail
+};
+DebugHooks &debug_hooks();
+// cudaMalloc through the allocation-failure hook.
+cudaError_t dev_alloc(void **p, size_t bytes);
+
 // FCC_DEBUG set to anything but "" or "0": print plan geometry and tuning steps.
 inline bool debug_enabled()
 {
@@ -100,6 +110,8 @@ struct Fp32Params {
     float *out_coef;        // nullable, [T][P][2K]
     float *out_corr;        // nullable, [T][P][I]
     unsigned *err;
+    long long wait_cycles;  // bound of every device-side wait (clock cycles)
+    int inject;             // test hook: 1 = CTA 0's first group withholds its first copy
 };
 
 // Batched FP32 form: one job = a run of consecutive tiles of one plan.

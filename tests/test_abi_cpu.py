@@ -57,3 +57,12 @@ def test_null_arguments_rejected_without_gpu(lib):
     d = binding.PlanDesc(4, None, 16000.0, 500, 343.0, 3.0, 4, 0, 0.999, 0, 0)
     assert lib.fcc_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1  # N not a power of two
     assert "power of two" in lib.fcc_last_error().decode()
+
+
+def test_debug_hooks_validate_arguments(lib):
+    assert lib.fcc_debug_set(99, 0) == 1
+    assert lib.fcc_debug_set(0, 10) == 1          # wait bound below 1000 cycles
+    assert lib.fcc_debug_set(1, -1) == 1
+    assert lib.fcc_debug_set(0, 5000) == 0
+    assert lib.fcc_debug_set(0, 0) == 0           # back to the default bound
+    assert lib.fcc_debug_set(2, 0) == 0
