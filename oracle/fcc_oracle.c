@@ -16,7 +16,7 @@
  *     rank-K operator W_K = U_K S_K V_K^H.  The SVD is this file's own complex
  *     one-sided (Hestenes) Jacobi iteration, checked against LAPACK in tests.
  *   - Sec. 2, Eq. 1 with alpha = 1: R = X_i X_j^*, R_hat = R / |R| (R_hat = 0
- *     where |R| = 0).
+ *     where |R| = 0); or_tdoa_smoothed runs Eq. 1's recursion for alpha < 1.
  *   - Eq. 2 / Eq. 4: y = 2 Re{ W_K x } with x = R_hat stacked over f.  With
  *     K = rank(W) this is eq. 2 itself (full-rank GCC-PHAT on the grid).
  *   - Sec. 2: tau* = argmax y (lowest index wins an exact tie) and a
@@ -311,6 +311,79 @@ void or_tdoa(const float *X, long long T, int M, int N, int I,
                 }
         }
         free(xr); free(xi); free(y);
+    }
+}
+
+/*
+ * Sec. 2, Eq. 1 with a smoothing factor alpha in (0, 1]: per pair and bin the
+ * cross-spectrum is estimated recursively over the frames,
+ *   R(t,f) = (1 - alpha) R(t-1,f) + alpha X_i(t,f) X_j(t,f)^*,
+ * starting from R0 (the state before the first frame: zero for a fresh stream),
+ * then the phase transform R_hat = R / |R| (0 where |R| = 0), y = 2 Re{ W x },
+ * argmax and the three-point refinement, as in or_tdoa.  The recurrence is
+ * sequential in t; pairs run in parallel.  R0 (may be NULL: zero) and R_end
+ * (may be NULL) are [P][B] complex, re/im interleaved, FP64.
+ */
+void or_tdoa_smoothed(const float *X, long long T, int M, int N, int I,
+                      const double *W_re, const double *W_im, const double *taus, double delta,
+                      double alpha, const double *R0, double *R_end,
+                      int *idx_out, double *peak_out, double *tau_out, double *y_out, int n_threads)
+{
+    int B = N / 2 + 1;
+    int P = M * (M - 1) / 2;
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = 1;
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+        double *Rr = (double *)malloc(sizeof(double) * B);
+        double *Ri = (double *)malloc(sizeof(double) * B);
+        double *xr = (double *)malloc(sizeof(double) * B);
+        double *xi = (double *)malloc(sizeof(double) * B);
+        double *y = (double *)malloc(sizeof(double) * I);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic)
+#endif
+        for (int p = 0; p < P; ++p) {
+            /* pair index p -> (i, j), i < j, lexicographic */
+            int i = 0, j = 0, q = p;
+            for (i = 0; i < M; ++i) {
+                if (q < M - 1 - i) { j = i + 1 + q; break; }
+                q -= M - 1 - i;
+            }
+            for (int f = 0; f < B; ++f) {
+                Rr[f] = R0 ? R0[2 * ((size_t)p * B + f)] : 0.0;
+                Ri[f] = R0 ? R0[2 * ((size_t)p * B + f) + 1] : 0.0;
+            }
+            for (long long t = 0; t < T; ++t) {
+                const float *Xt = X + (size_t)t * M * B * 2;
+                for (int f = 0; f < B; ++f) {
+                    double ar = Xt[2 * ((size_t)i * B + f)], ai = Xt[2 * ((size_t)i * B + f) + 1];
+                    double br = Xt[2 * ((size_t)j * B + f)], bi = Xt[2 * ((size_t)j * B + f) + 1];
+                    double cr = ar * br + ai * bi; /* X_i X_j^* */
+                    double ci = ai * br - ar * bi;
+                    Rr[f] = (1.0 - alpha) * Rr[f] + alpha * cr;
+                    Ri[f] = (1.0 - alpha) * Ri[f] + alpha * ci;
+                    double mag = sqrt(Rr[f] * Rr[f] + Ri[f] * Ri[f]);
+                    xr[f] = mag > 0 ? Rr[f] / mag : 0.0;
+                    xi[f] = mag > 0 ? Ri[f] / mag : 0.0;
+                }
+                or_correlate(I, B, W_re, W_im, xr, xi, y);
+                int k = or_argmax(y, I);
+                size_t o = (size_t)t * P + p;
+                idx_out[o] = k;
+                peak_out[o] = y[k];
+                tau_out[o] = or_parabola(y, I, k, taus[k], delta);
+                if (y_out)
+                    memcpy(y_out + o * I, y, sizeof(double) * I);
+            }
+            if (R_end)
+                for (int f = 0; f < B; ++f) {
+                    R_end[2 * ((size_t)p * B + f)] = Rr[f];
+                    R_end[2 * ((size_t)p * B + f) + 1] = Ri[f];
+                }
+        }
+        free(Rr); free(Ri); free(xr); free(xi); free(y);
     }
 }
 

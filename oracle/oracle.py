@@ -76,6 +76,10 @@ def _load():
                                     ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _ip, _dp, _dp,
                                     _dp, ctypes.c_int]
             lib.or_tdoa.restype = None
+            lib.or_tdoa_smoothed.argtypes = [_fp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                             _ip, _dp, _dp, _dp, ctypes.c_int]
+            lib.or_tdoa_smoothed.restype = None
             lib.or_mlp_nparams.argtypes = [ctypes.c_int, ctypes.c_int]
             lib.or_mlp_nparams.restype = ctypes.c_longlong
             lib.or_mlp_forward.argtypes = [_dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _dp, _dp]
@@ -235,6 +239,34 @@ def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: b
 # ----------------------------------------------------------------------------
 # learned TDoA head (not in the paper): FP64 reference of the MLP
 # ----------------------------------------------------------------------------
+def tdoa_smoothed(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, alpha: float, R0=None,
+                  want_y: bool = False, threads: int | None = None):
+    """The pipeline with Eq. 1's recursive cross-spectrum for a smoothing factor
+    alpha in (0, 1]: R(t) = (1 - alpha) R(t-1) + alpha X_i X_j^*, from R0 ([P, B]
+    complex, None = zero), then R_hat = R / |R| and the rest as `tdoa`.
+    Returns (idx, peak, tau_hat, y or None, R_end [P, B] complex128)."""
+    X = np.ascontiguousarray(X, np.complex64)
+    T, M, B = X.shape
+    N = 2 * (B - 1)
+    I = W.shape[0]
+    assert W.shape[1] == B and len(taus) == I
+    P = M * (M - 1) // 2
+    wr, wi = np.ascontiguousarray(W.real), np.ascontiguousarray(W.imag)
+    taus = np.ascontiguousarray(taus, np.float64)
+    r0 = None if R0 is None else np.ascontiguousarray(np.asarray(R0, np.complex128).reshape(P, B))
+    r_end = np.empty((P, B), np.complex128)
+    idx = np.empty((T, P), np.int32)
+    peak = np.empty((T, P))
+    tau = np.empty((T, P))
+    y = np.empty((T, P, I)) if want_y else None
+    nt = max_threads() if threads is None else int(threads)
+    _load().or_tdoa_smoothed(X.ctypes.data_as(_fp), T, M, N, I, _d(wr), _d(wi), _d(taus), float(delta),
+                             float(alpha), None if r0 is None else r0.ctypes.data_as(_dp),
+                             r_end.ctypes.data_as(_dp), idx.ctypes.data_as(_ip), _d(peak), _d(tau),
+                             _d(y) if want_y else None, nt)
+    return idx, peak, tau, y, r_end
+
+
 def mlp_nparams(nin: int, H: int) -> int:
     return int(_load().or_mlp_nparams(nin, H))
 
