@@ -33,7 +33,9 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            "fcc_batch_create", "fcc_batch_destroy", "fcc_batch_info", "fcc_batch_array_info", "fcc_batch_bind",
            "fcc_batch_run", "fcc_batch_sync",
            # include/fcc_debug.h
-           "fcc_debug_set"]
+           "fcc_debug_set",
+           # include/fcc_smooth.h
+           "fcc_smooth_workspace", "fcc_tdoa_smoothed"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -137,6 +139,11 @@ def lib():
         L.fcc_batch_run.argtypes = [_vp, _vp]
         L.fcc_debug_set.argtypes = [ctypes.c_int, ctypes.c_longlong]
         L.fcc_debug_set.restype = ctypes.c_int
+        L.fcc_smooth_workspace.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.fcc_smooth_workspace.restype = ctypes.c_int
+        L.fcc_tdoa_smoothed.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_double, _vp, _vp, ctypes.c_longlong,
+                                        _vp, _vp, _vp, _vp, _vp]
+        L.fcc_tdoa_smoothed.restype = ctypes.c_int
         L.fcc_batch_sync.argtypes = [_vp, _vp]
         for name in ("fcc_plan_geometry", "fcc_plan_autotune", "fcc_batch_create", "fcc_batch_info",
                      "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):
@@ -309,6 +316,37 @@ class Plan:
         check(lib().fcc_tdoa_learned(self._h, mlp._h, _ptr(X), T, float(threshold), _ptr(out["lag_idx"]),
                                      _ptr(out["peak"]), _ptr(out["tau_fcc"]), _ptr(out["coeffs"]), _ptr(out["tau"]),
                                      _ptr(out.get("conf")), _stream(stream, dev)), "fcc_tdoa_learned")
+        return out
+
+    def smooth_workspace(self, T: int) -> int:
+        b = ctypes.c_longlong()
+        check(lib().fcc_smooth_workspace(self._h, int(T), ctypes.byref(b)), "fcc_smooth_workspace")
+        return b.value
+
+    def tdoa_smoothed(self, X, alpha: float, state=None, tau_hat: bool = True, coeffs: bool = False,
+                      work=None, stream=None, out=None):
+        """fcc_tdoa_smoothed: Eq. 1's recursive cross-spectrum with factor alpha,
+        then FCC.  `state`: complex64 [P, B] device tensor holding R(0) on entry
+        and R(T) on return (None: a fresh stream, final state dropped)."""
+        import torch
+        self._check_spectra(X)
+        T, dev = X.shape[0], X.device
+        if state is not None and (state.dtype != torch.complex64 or tuple(state.shape) != (self.P, self.B)
+                                  or not state.is_contiguous()):
+            raise ValueError(f"state must be contiguous complex64 [{self.P}, {self.B}]")
+        if work is None:
+            nbytes = self.smooth_workspace(T)
+            work = torch.empty(max(nbytes, 8), dtype=torch.uint8, device=dev)
+        if out is None:
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, device=dev),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, device=dev)}
+            if tau_hat:
+                out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, device=dev)
+            if coeffs:
+                out["coeffs"] = torch.empty((T, self.P, 2 * self.K), dtype=torch.float32, device=dev)
+        check(lib().fcc_tdoa_smoothed(self._h, _ptr(X), T, float(alpha), _ptr(state), _ptr(work), work.numel(),
+                                      _ptr(out["lag_idx"]), _ptr(out["peak"]), _ptr(out.get("tau_hat")),
+                                      _ptr(out.get("coeffs")), _stream(stream, dev)), "fcc_tdoa_smoothed")
         return out
 
     def geometry(self) -> dict:

@@ -164,6 +164,7 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_err);
     cudaFree(p->d_tc_bases);
     cudaFree(p->d_tc_peq);
+    cudaFree(p->d_smooth_basis);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->d_stage[b]);
         cudaFree(p->d_stage_idx[b]);

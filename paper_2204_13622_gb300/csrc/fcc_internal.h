@@ -181,6 +181,7 @@ struct fcc_plan {
     // GCC baseline workspace, created lazily
     void *gcc_state = nullptr;
     // tensor-core (BF16 / FP16) path
+    float *d_smooth_basis = nullptr;   // smoothed path: [Q+1][2 kh], created on first use
     void *d_tc_bases = nullptr;
     float *d_tc_peq = nullptr;
     int tc_F = 0;
