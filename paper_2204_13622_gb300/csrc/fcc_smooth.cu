@@ -5,8 +5,8 @@
 // phase transform acts on each pair's smoothed R, and R carries state from frame
 // to frame.  The frames are cut into chunks and the linear recursion is solved
 // exactly in three passes:
-//   1. chunk_sums_kernel  per chunk and (pair, bin): the recursion run from zero
-//      over the chunk's frames (L_c);
+//   1. chunk_sums_kernel  per chunk, one thread per bin holding all pairs'
+//      running sums: the recursion run from zero over the chunk's frames (L_c);
 //   2. carry_kernel       per (pair, bin), over the chunks in order: the state
 //      entering chunk c, S_c = (1 - alpha)^len(c-1) S_{c-1} + L_{c-1} from the
 //      caller's initial state, and the state after the last frame (returned);
@@ -49,29 +49,44 @@ struct SmoothParams {
     long long wait_cycles;
 };
 
-// Pass 1: the recursion run from zero over each chunk, per (pair, bin).
-__global__ void chunk_sums_kernel(const float2 *X, long long T, int M, int B, int chunk, int n_chunks, float alpha,
-                                  float beta, float2 *sums)
+// Pass 1: the recursion run from zero over each chunk.  One CTA per chunk, one
+// thread per bin f: per frame it loads the M microphones' X(f) once (coalesced
+// across the CTA, so each frame is read from HBM once) and updates the running
+// sums of all P pairs in registers.
+template <int M>
+__global__ void chunk_sums_kernel(const float2 *X, long long T, int B, int chunk, float alpha, float beta,
+                                  float2 *sums)
 {
-    const int P = M * (M - 1) / 2;
-    const int c = blockIdx.y;
+    constexpr int P = M * (M - 1) / 2;
+    const int c = blockIdx.x, f = threadIdx.x;
+    if (f >= B) return;
     const long long t0 = (long long)c * chunk, t1 = min(T, t0 + chunk);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P * B; e += gridDim.x * blockDim.x) {
-        const int p = e / B, f = e - p * B;
-        int i = 0, q = p;
-        while (q >= M - 1 - i) {
-            q -= M - 1 - i;
-            ++i;
+    f2 acc[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) acc[q] = 0ull;
+    const f2 beta2 = pk(beta, beta);
+    const float2 *xp = X + (size_t)t0 * M * B + f;
+    for (long long t = t0; t < t1; ++t, xp += (size_t)M * B) {
+        float2 x[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) x[m] = __ldg(xp + (size_t)m * B);
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const f2 xa = pk(x[i].x, x[i].y), xw = pk(x[i].y, x[i].x);
+#pragma unroll
+            for (int j = i + 1; j < M; ++j, ++q) {
+                // alpha x_i x_j^* = (xr yr + xi yi, xi yr - xr yi) alpha
+                const f2 yr = pk(alpha * x[j].x, alpha * x[j].x), yi = pk(alpha * x[j].y, -alpha * x[j].y);
+                acc[q] = fma2(beta2, acc[q], fma2(xw, yi, mul2(xa, yr)));
+            }
         }
-        const int j = i + 1 + q;
-        float2 acc = make_float2(0.f, 0.f);
-        for (long long t = t0; t < t1; ++t) {
-            const float2 a = X[((size_t)t * M + i) * B + f], b = X[((size_t)t * M + j) * B + f];
-            const float cr = fmaf(a.x, b.x, a.y * b.y), ci = fmaf(a.y, b.x, -(a.x * b.y));
-            acc.x = fmaf(beta, acc.x, alpha * cr);
-            acc.y = fmaf(beta, acc.y, alpha * ci);
-        }
-        sums[((size_t)c * P + p) * B + f] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        float re, im;
+        upk(acc[q], re, im);
+        sums[((size_t)c * P + q) * B + f] = make_float2(re, im);
     }
 }
 
@@ -223,14 +238,28 @@ __global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constan
                     w[4 * v + 2] = e.z;
                     w[4 * v + 3] = e.w;
                 }
+                // packed operands: x as (re, im) and (im, re), y as (re, re) and (im, -im),
+                // so x y^* is one FMUL2 + one FFMA2 (scaled by alpha on the y side)
+                f2 xa[2][2], xw[2][2], yr[2][2], yi[2][2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    xa[u][0] = pk(xf[u].x, xf[u].y);
+                    xw[u][0] = pk(xf[u].y, xf[u].x);
+                    xa[u][1] = pk(xb[u].x, xb[u].y);
+                    xw[u][1] = pk(xb[u].y, xb[u].x);
+                    yr[u][0] = pk(p.alpha * yf[u].x, p.alpha * yf[u].x);
+                    yi[u][0] = pk(p.alpha * yf[u].y, -p.alpha * yf[u].y);
+                    yr[u][1] = pk(p.alpha * yb[u].x, p.alpha * yb[u].x);
+                    yi[u][1] = pk(p.alpha * yb[u].y, -p.alpha * yb[u].y);
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 x = xf[q >> 1], y = yf[q & 1], x2 = xb[q >> 1], y2 = yb[q & 1];
-                    // Eq. 1 at f and N/2 - f, then the phase transform of R
-                    const f2 a = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
-                    const f2 b = pk(fmaf(x2.x, y2.x, x2.y * y2.y), fmaf(x2.y, y2.x, -(x2.x * y2.y)));
-                    R[q][j][0] = fma2(beta2, R[q][j][0], mul2(alpha2, a));
-                    R[q][j][1] = fma2(beta2, R[q][j][1], mul2(alpha2, b));
+                    const int ix = q >> 1, iy = q & 1;
+                    // Eq. 1 at f and N/2 - f (alpha X_i X_j^*), then the phase transform of R
+                    const f2 a = fma2(xw[ix][0], yi[iy][0], mul2(xa[ix][0], yr[iy][0]));
+                    const f2 b = fma2(xw[ix][1], yi[iy][1], mul2(xa[ix][1], yr[iy][1]));
+                    R[q][j][0] = fma2(beta2, R[q][j][0], a);
+                    R[q][j][1] = fma2(beta2, R[q][j][1], b);
                     float r0x, r0y, r1x, r1y;
                     upk(R[q][j][0], r0x, r0y);
                     upk(R[q][j][1], r1x, r1y);
@@ -495,9 +524,15 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
     const int PB = in.P * in.B;
     // pass 1 and pass 2
     {
-        dim3 grid1((unsigned)std::min(64, (PB + 255) / 256), (unsigned)g.n_chunks);
-        chunk_sums_kernel<<<grid1, 256, 0, s>>>(static_cast<const float2 *>(d_spectra), T, in.M, in.B, g.chunk,
-                                                 g.n_chunks, a, b, work);
+        const int threads = (in.B + 31) / 32 * 32;
+        const float2 *X = static_cast<const float2 *>(d_spectra);
+        switch (in.M) {
+        case 2: chunk_sums_kernel<2><<<g.n_chunks, threads, 0, s>>>(X, T, in.B, g.chunk, a, b, work); break;
+        case 4: chunk_sums_kernel<4><<<g.n_chunks, threads, 0, s>>>(X, T, in.B, g.chunk, a, b, work); break;
+        case 6: chunk_sums_kernel<6><<<g.n_chunks, threads, 0, s>>>(X, T, in.B, g.chunk, a, b, work); break;
+        case 8: chunk_sums_kernel<8><<<g.n_chunks, threads, 0, s>>>(X, T, in.B, g.chunk, a, b, work); break;
+        default: return fail(FCC_ERR_UNSUPPORTED, "the smoothed path needs 2, 4, 6 or 8 mics");
+        }
         carry_kernel<<<(PB + 127) / 128, 128, 0, s>>>(work, PB, g.n_chunks, T, g.chunk, b,
                                                       static_cast<const float2 *>(d_state),
                                                       static_cast<float2 *>(d_state));
