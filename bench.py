@@ -376,6 +376,18 @@ def fp32_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float:
             + 5.0 * M * B / P)
 
 
+def smooth_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float:
+    """FP32 operations per pair-frame of one smoothed step (Eq. 1; FMA = 1): the
+    chunk-sum pass (cross spectrum 4 + update 2 per bin) and the main pass
+    (cross spectrum 4, update 2 and phase transform 6 per bin: power-of-two
+    scaling 2, |R|^2 2, final scaling 2), then the fold, the projections and the
+    reconstruction as the unsmoothed kernel.  Rsqrt and the carry scan are not
+    counted."""
+    B, Q = N // 2 + 1, N // 4
+    center = (I - 1) // 2
+    return (6 * B + 12 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (4 * (KE + KO) + 2))
+
+
 def alu_roofline(ops: float, ms: float, kernel: str) -> dict:
     achieved = ops / (ms / 1000.0)
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_OPS / 1e12, "unit": "TFLOP/s",
@@ -511,7 +523,7 @@ def run_smoothed(args, rank, world, local):
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     ms = sum(per) / args.steps
     ms_max = max_over_ranks(ms, distributed, dev)
-    bytes_alg = T * (w.M * w.B * 8) + T * P * 12
+    bytes_alg = 2 * T * (w.M * w.B * 8) + T * P * 12
     peak, psrc = _peak_hbm()
     res = None
     if rank == 0:
@@ -534,11 +546,13 @@ def run_smoothed(args, rank, world, local):
                "config": {"workload": f"{w.name}, Eq. 1 smoothing alpha={args.alpha}", "frames": T, "pairs": P,
                           "state": "carried from step to step",
                           "l2": "inputs larger than L2; no flush"},
-               "roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1000.0) / 1e9, "peak": peak,
-                            "unit": "GB/s", "frac": bytes_alg / (ms / 1000.0) / 1e9 / peak, "traffic": None,
-                            "kernel": "chunk_sums_kernel + carry_kernel + fcc_smooth_kernel",
-                            "bytes_per_launch": bytes_alg, "peak_source": psrc,
-                            "note": "algorithmic bytes read the spectra once; the three passes read them twice"},
+               "roofline": dict(alu_roofline(T * P * smooth_ops_per_pair_frame(w.M, w.N, plan.K_even, plan.K_odd, plan.I),
+                                             ms, "chunk_sums_kernel + carry_kernel + fcc_smooth_kernel (one step)"),
+                                traffic=None,
+                                hbm={"achieved": bytes_alg / (ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+                                     "frac": bytes_alg / (ms / 1000.0) / 1e9 / peak, "bytes_per_step": bytes_alg,
+                                     "peak_source": psrc,
+                                     "note": "the spectra read twice (chunk sums, main pass) plus the outputs"}),
                "accuracy_vs_oracle": {"pair_frames": int(gi.size), "argmax_agreement": float((gi == idx).mean())},
                "cpu_baseline": {"value": n * P / t_or, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
                                 "sample": f"first {n} frames, FP64 recursion (pairs in parallel)"},

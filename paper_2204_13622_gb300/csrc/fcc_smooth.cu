@@ -10,12 +10,14 @@
 //   2. carry_kernel       per (pair, bin), over the chunks in order: the state
 //      entering chunk c, S_c = (1 - alpha)^len(c-1) S_{c-1} + L_{c-1} from the
 //      caller's initial state, and the state after the last frame (returned);
-//   3. fcc_smooth_kernel  per chunk: one warp per 2x2 pair slot, lane l owns the
-//      fold records l, l + 32, ... of its four pairs and keeps their smoothed R
-//      (both bins of each record) in registers across the chunk's frames; per
-//      frame it updates R, applies the phase transform, folds (Eq. 8) and
-//      projects (Eqs. 7, 9); the 32 lanes reduce the projections with shuffles
-//      and reconstruct the lag grid, argmax and refinement as the FP32 path.
+//   3. fcc_smooth_kernel  per chunk: one warp per 2x2 pair slot.  Lane l owns
+//      the fold records l, l + 32, ... of its four pairs and keeps their
+//      smoothed R (both bins of each record, as R / alpha) in registers across
+//      the chunk's frames; per frame it updates R, applies the phase transform
+//      and folds (Eq. 8) into the warp's shared-memory rows.  Then lane (q, i)
+//      projects pair q's rows onto coefficient(s) i (Eqs. 7, 9) with no
+//      cross-lane reduction, and 8 lanes per pair reconstruct the lag grid,
+//      argmax and refinement as the FP32 path.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -27,7 +29,7 @@
 namespace fcc {
 namespace {
 
-constexpr int kSmoothStages = 4;
+constexpr int kSmoothStages = 2;
 
 struct SmoothParams {
     const float2 *spectra;  // [T][M][B]
@@ -36,7 +38,7 @@ struct SmoothParams {
     int chunk, n_chunks;    // frames per chunk
     float alpha, beta;      // beta = 1 - alpha
     const float2 *carry;    // [n_chunks][P][B]: the state entering each chunk
-    const float *basis;     // [Q + 1][2 KH]: even weights, then odd (zero at N/4)
+    const float *basis;     // [2 KH][QP]: even bases' weights over records 0..Q, then odd (zero at Q and in the padding)
     const float *recon;     // [center + 1][KH][4]
     const Slot *slots;
     int center, I, KE, KO;
@@ -91,55 +93,100 @@ __global__ void chunk_sums_kernel(const float2 *X, long long T, int B, int chunk
 }
 
 // Pass 2: the state entering each chunk (written over the chunk sums) and the
-// state after the last frame.
+// state after the last frame.  The chunk sums are loaded kCarryBatch at a time
+// ahead of the dependent updates, so the loads overlap.
+constexpr int kCarryBatch = 16;
 __global__ void carry_kernel(float2 *sums_to_carry, int PB, int n_chunks, long long T, int chunk, float beta,
                              const float2 *state_in, float2 *state_out)
 {
+    const float decay_full = powf(beta, (float)chunk);
+    const long long last_len = T - (long long)(n_chunks - 1) * chunk;
+    const float decay_last = powf(beta, (float)last_len);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < PB; e += gridDim.x * blockDim.x) {
         float2 S = state_in ? state_in[e] : make_float2(0.f, 0.f);
-        for (int c = 0; c < n_chunks; ++c) {
-            const long long len = min((long long)chunk, T - (long long)c * chunk);
-            const float decay = powf(beta, (float)len);
-            const float2 Lc = sums_to_carry[(size_t)c * PB + e];
-            sums_to_carry[(size_t)c * PB + e] = S;
-            S.x = fmaf(decay, S.x, Lc.x);
-            S.y = fmaf(decay, S.y, Lc.y);
+        for (int c0 = 0; c0 < n_chunks; c0 += kCarryBatch) {
+            float2 L[kCarryBatch];
+#pragma unroll
+            for (int u = 0; u < kCarryBatch; ++u)
+                if (c0 + u < n_chunks) L[u] = sums_to_carry[(size_t)(c0 + u) * PB + e];
+#pragma unroll
+            for (int u = 0; u < kCarryBatch; ++u)
+                if (c0 + u < n_chunks) {
+                    const float decay = c0 + u == n_chunks - 1 ? decay_last : decay_full;
+                    sums_to_carry[(size_t)(c0 + u) * PB + e] = S;
+                    S.x = fmaf(decay, S.x, L[u].x);
+                    S.y = fmaf(decay, S.y, L[u].y);
+                }
         }
         if (state_out) state_out[e] = S;
     }
 }
 
-// R_hat = R / |R| (0 where R = 0; non-finite R flags the error word).
-__device__ __forceinline__ f2 unit_of(float rx, float ry, bool &bad)
-{
-    const float s = fmaf(rx, rx, ry * ry);
-    if (s >= FLT_MIN && s <= FLT_MAX) {
-        const float r = rsqrtf(s);
-        return mul2(pk(rx, ry), pk(r, r));
+// Shared-memory layout of fcc_smooth_kernel, the same on host and device.
+// Per warp: 8 rows (2 q + d: pair q's folded x_s for d = 0, x_d for d = 1) of
+// QP = Q + 1 records rounded up to 4, at a row stride of QP * 8 + 16 bytes (an
+// odd multiple of 16 modulo 128, so the 8 rows at one record fall into 8
+// different 16-byte bank groups), then the pairs' 2 KH coefficients, then the
+// four pairs' smoothed R at the lone bin N/4.
+struct SmoothLayout {
+    int QP, row_bytes, warp_bytes;
+    size_t basis_off, recon_off, warps_off, stages_off, stage_bytes, total;
+    __host__ __device__ SmoothLayout(int Q, int KH, int center, int M, int B, int n_warps)
+    {
+        QP = (Q + 4) & ~3;
+        row_bytes = QP * 8 + 16;
+        warp_bytes = (8 * row_bytes + 4 * 2 * KH * 8 + 4 * 8 + 127) & ~127;
+        basis_off = 128 + 8 * sizeof(Slot);
+        recon_off = basis_off + (size_t)2 * KH * QP * 4;
+        warps_off = (recon_off + (size_t)(center + 1) * 4 * KH * 4 + 127) & ~(size_t)127;
+        stages_off = warps_off + (size_t)n_warps * warp_bytes;
+        stage_bytes = ((size_t)M * B * 8 + 127) & ~(size_t)127;
+        total = stages_off + kSmoothStages * stage_bytes;
     }
-    bool b2 = false;
-    const float2 u = unit_phase_slow(make_float2(rx, ry), b2);
-    bad = bad || b2;
-    return pk(u.x, u.y);
+};
+
+// Pass 3.  One warp per 2x2 pair slot; per frame:
+//   state    lane l owns records l, l + 32, ... (both bins f and N/2 - f) of the
+//            slot's four pairs and keeps their R in registers: Eq. 1 update,
+//            R_hat = R / |R|, fold (Eq. 8), x_s and x_d written to the warp's rows;
+//   project  lane (q, i) = (l / 8, l % 8) forms coefficient(s) i * CPL.. of pair q
+//            over all records (Eqs. 7, 9): no cross-lane reduction;
+//   search   8 lanes per pair split the lag steps of the reconstruction, then
+//            argmax and refinement as the FP32 path.
+// R / |R| without a branch: R is first scaled by the power of two that brings
+// max(|Re R|, |Im R|) into [1, 2) (the scale is clamped to >= 2^-126, so the
+// largest finite R lands in [2, 4)), which keeps |R|^2 normal for any finite
+// R.  R = 0 gives 0 (the rsqrt argument is floored at FLT_MIN); a non-finite R
+// flags the error word.
+__device__ __forceinline__ f2 unit_scaled(float rx, float ry, bool &bad)
+{
+    const int eb = (int)(__float_as_uint(fmaxf(fabsf(rx), fabsf(ry))) & 0x7f800000u);
+    const float sc = __int_as_float(max(0x7f000000 - eb, 0x00800000));
+    const f2 ab = mul2(pk(rx, ry), pk(sc, sc));
+    float a, b;
+    upk(ab, a, b);
+    const float s = fmaf(a, a, b * b);
+    bad = bad || !(s < 64.f);
+    const float r = rsqrtf(fmaxf(s, FLT_MIN));
+    return mul2(ab, pk(r, r));
 }
 
 template <int KH, int RS>
-__global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constant__ SmoothParams p)
+__global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constant__ SmoothParams p)
 {
+    constexpr int CPL = KH > 4 ? 2 : 1;  // coefficients per projecting lane
     extern __shared__ __align__(128) unsigned char smem[];
-    const int frame_bytes = p.M * p.B * 8;
-    const size_t stage_bytes = ((size_t)frame_bytes + 127) & ~(size_t)127;
+    const SmoothLayout Ly(p.Q, KH, p.center, p.M, p.B, p.n_slots);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *freed = full + kSmoothStages;
     Slot *slots = reinterpret_cast<Slot *>(smem + 128);
-    float *basis = reinterpret_cast<float *>(smem + 128 + 8 * sizeof(Slot));
-    const int nbasis = (p.Q + 1) * 2 * KH;
-    float *recon = basis + nbasis;
-    const size_t tab_end = (128 + 8 * sizeof(Slot) + (size_t)(nbasis + (p.center + 1) * 4 * KH) * 4 + 127) & ~(size_t)127;
-    unsigned char *stages = smem + tab_end;
+    float *basis = reinterpret_cast<float *>(smem + Ly.basis_off);  // [2 KH][QP]
+    float *recon = reinterpret_cast<float *>(smem + Ly.recon_off);
+    unsigned char *stages = smem + Ly.stages_off;
+    const int frame_bytes = p.M * p.B * 8;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Q = p.Q, B = p.B, M = p.M;
+    const int Q = p.Q, B = p.B, QP = Ly.QP;
     const unsigned FULLM = 0xffffffffu;
     const int nw = p.n_slots;  // one warp per slot
     if (threadIdx.x == 0) {
@@ -150,12 +197,19 @@ __global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constan
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
-    for (int e = threadIdx.x; e < nbasis; e += blockDim.x) basis[e] = p.basis[e];
+    for (int e = threadIdx.x; e < 2 * KH * QP; e += blockDim.x) basis[e] = p.basis[e];
     for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
+    unsigned char *wreg = smem + Ly.warps_off + (size_t)warp * Ly.warp_bytes;
+    // the padding records Q + 1 .. QP - 1 stay zero (their basis entries are zero too)
+    const int npad = QP - Q - 1;
+    for (int e = lane; e < 8 * npad; e += 32)
+        reinterpret_cast<float2 *>(wreg + (size_t)(e / npad) * Ly.row_bytes)[Q + 1 + e % npad] = make_float2(0.f, 0.f);
     fence_proxy_async();
     __syncthreads();
 
     const Slot sl = slots[warp];
+    float2 *zbuf = reinterpret_cast<float2 *>(wreg + 8 * Ly.row_bytes);  // [4][2 KH]
+    f2 *Rl = reinterpret_cast<f2 *>(zbuf + 4 * 2 * KH);                 // [4], lane 0's
     bool bad = false, failed = false;
     // This CTA's frames as one sequence g = i * chunk + k over its chunks
     // c_i = blockIdx.x + i * gridDim.x (only the global last chunk can be short,
@@ -173,19 +227,23 @@ __global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constan
     auto issue = [&](long long g) {
         const int s = (int)(g % kSmoothStages);
         mbar_arrive_expect_tx(&full[s], (unsigned)frame_bytes);
-        bulk_g2s(stages + (size_t)s * stage_bytes,
+        bulk_g2s(stages + (size_t)s * Ly.stage_bytes,
                  reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)frame_of(g) * frame_bytes,
                  (unsigned)frame_bytes, &full[s]);
     };
     long long issued = 0, g = 0;
     if (threadIdx.x == 0)
         for (; issued < kSmoothStages && issued < total_g; ++issued) issue(issued);
+    const f2 beta2 = pk(p.beta, p.beta);
     for (int ci = 0; ci < my_chunks && !failed; ++ci) {
         const int c = (int)blockIdx.x + ci * (int)gridDim.x;
         const long long t0 = (long long)c * p.chunk;
         const int len = (int)min((long long)p.chunk, p.T - t0);
-        // the state entering this chunk: R of the slot's four pairs at this lane's records
-        f2 R[4][RS][2], Rl[4];
+        // the state entering this chunk, R of the slot's four pairs at this lane's
+        // records, held as R / alpha: then R / alpha <- beta R / alpha + X_i X_j^*
+        // needs no scaling per frame, and the phase transform is unchanged
+        const f2 ia2 = pk(1.f / p.alpha, 1.f / p.alpha);
+        f2 R[4][RS][2];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int pq = sl.pair[q] >= 0 ? sl.pair[q] : 0;
@@ -194,29 +252,36 @@ __global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constan
             for (int j = 0; j < RS; ++j) {
                 const int fp = lane + 32 * j;
                 const float2 u = cs[fp], v = cs[2 * Q - fp];
-                R[q][j][0] = pk(u.x, u.y);
-                R[q][j][1] = pk(v.x, v.y);
+                R[q][j][0] = mul2(ia2, pk(u.x, u.y));
+                R[q][j][1] = mul2(ia2, pk(v.x, v.y));
             }
-            const float2 w = cs[Q];
-            Rl[q] = pk(w.x, w.y);
+            if (lane == 0) {
+                const float2 w = cs[Q];
+                Rl[q] = mul2(ia2, pk(w.x, w.y));
+            }
         }
-        const f2 beta2 = pk(p.beta, p.beta), alpha2 = pk(p.alpha, p.alpha);
+#pragma unroll 1
         for (int k = 0; k < len; ++k, ++g) {
+            // refill the stage of frame g - 1 with frame g - 1 + S once every warp released it
+            if (threadIdx.x == 0 && g > 0 && issued < total_g) {
+                const long long h = g - 1;
+                if (!mbar_wait(&freed[h % kSmoothStages], (unsigned)(h / kSmoothStages) & 1u, p.wait_cycles)) {
+                    atomicOr(p.err, kErrTimeout);
+                } else {
+                    issue(issued);
+                    ++issued;
+                }
+            }
             const int s = (int)(g % kSmoothStages);
-            const unsigned par = (unsigned)(g / kSmoothStages) & 1u;
-            if (!mbar_wait(&full[s], par, p.wait_cycles)) {
+            if (!mbar_wait(&full[s], (unsigned)(g / kSmoothStages) & 1u, p.wait_cycles)) {
                 failed = true;
                 break;
             }
-            const unsigned char *st = stages + (size_t)s * stage_bytes;
-            f2 accE[4][KH], accO[4][KH];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int v = 0; v < KH; ++v) accE[q][v] = accO[q][v] = 0ull;
+            const unsigned char *st = stages + (size_t)s * Ly.stage_bytes;
             const float2 *row[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) row[r] = reinterpret_cast<const float2 *>(st + (size_t)sl.mic[r] * B * 8);
+            // ---- state: Eq. 1, phase transform, fold (Eq. 8)
 #pragma unroll
             for (int j = 0; j < RS; ++j) {
                 const int fp = lane + 32 * j;
@@ -228,117 +293,68 @@ __global__ void __launch_bounds__(256, 1) fcc_smooth_kernel(const __grid_constan
                     yf[u] = row[2 + u][fp];
                     yb[u] = row[2 + u][2 * Q - fp];
                 }
-                const float4 *bw = reinterpret_cast<const float4 *>(basis + (size_t)fp * 2 * KH);
-                float w[2 * KH];
-#pragma unroll
-                for (int v = 0; v < KH / 2; ++v) {
-                    const float4 e = bw[v];
-                    w[4 * v] = e.x;
-                    w[4 * v + 1] = e.y;
-                    w[4 * v + 2] = e.z;
-                    w[4 * v + 3] = e.w;
-                }
-                // packed operands: x as (re, im) and (im, re), y as (re, re) and (im, -im),
-                // so x y^* is one FMUL2 + one FFMA2 (scaled by alpha on the y side)
-                f2 xa[2][2], xw[2][2], yr[2][2], yi[2][2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    xa[u][0] = pk(xf[u].x, xf[u].y);
-                    xw[u][0] = pk(xf[u].y, xf[u].x);
-                    xa[u][1] = pk(xb[u].x, xb[u].y);
-                    xw[u][1] = pk(xb[u].y, xb[u].x);
-                    yr[u][0] = pk(p.alpha * yf[u].x, p.alpha * yf[u].x);
-                    yi[u][0] = pk(p.alpha * yf[u].y, -p.alpha * yf[u].y);
-                    yr[u][1] = pk(p.alpha * yb[u].x, p.alpha * yb[u].x);
-                    yi[u][1] = pk(p.alpha * yb[u].y, -p.alpha * yb[u].y);
-                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int ix = q >> 1, iy = q & 1;
-                    // Eq. 1 at f and N/2 - f (alpha X_i X_j^*), then the phase transform of R
-                    const f2 a = fma2(xw[ix][0], yi[iy][0], mul2(xa[ix][0], yr[iy][0]));
-                    const f2 b = fma2(xw[ix][1], yi[iy][1], mul2(xa[ix][1], yr[iy][1]));
+                    const float2 x0 = xf[q >> 1], x1 = xb[q >> 1], y0 = yf[q & 1], y1 = yb[q & 1];
+                    // x y^* = (xr yr + xi yi, xi yr - xr yi), as one FMUL2 + one FFMA2
+                    const f2 a = fma2(pk(x0.y, x0.x), pk(y0.y, -y0.y), mul2(pk(x0.x, x0.y), pk(y0.x, y0.x)));
+                    const f2 b = fma2(pk(x1.y, x1.x), pk(y1.y, -y1.y), mul2(pk(x1.x, x1.y), pk(y1.x, y1.x)));
                     R[q][j][0] = fma2(beta2, R[q][j][0], a);
                     R[q][j][1] = fma2(beta2, R[q][j][1], b);
                     float r0x, r0y, r1x, r1y;
                     upk(R[q][j][0], r0x, r0y);
                     upk(R[q][j][1], r1x, r1y);
-                    const f2 ua = unit_of(r0x, r0y, bad), ub = unit_of(r1x, r1y, bad);
-                    const f2 xs = add2(ua, ub), xd = sub2(ua, ub);  // Eq. 8
-#pragma unroll
-                    for (int v = 0; v < KH; ++v) {
-                        accE[q][v] = fma2(pk(w[v], w[v]), xs, accE[q][v]);
-                        accO[q][v] = fma2(pk(w[KH + v], w[KH + v]), xd, accO[q][v]);
-                    }
+                    const f2 ua = unit_scaled(r0x, r0y, bad), ub = unit_scaled(r1x, r1y, bad);
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[fp] = add2(ua, ub);
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[fp] = sub2(ua, ub);
                 }
             }
             if (lane == 0) {
-                // the lone bin N/4: x_s = R_hat(N/4), no odd part (Eq. 8)
-                const float *bq = basis + (size_t)Q * 2 * KH;
+                // the lone bin N/4: x_s = R_hat(N/4), x_d = 0 (Eq. 8)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float2 x = row[q >> 1][Q], y = row[2 + (q & 1)][Q];
                     const f2 a = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
-                    Rl[q] = fma2(beta2, Rl[q], mul2(alpha2, a));
+                    Rl[q] = fma2(beta2, Rl[q], a);
                     float rx, ry;
                     upk(Rl[q], rx, ry);
-                    const f2 ua = unit_of(rx, ry, bad);
-#pragma unroll
-                    for (int v = 0; v < KH; ++v) accE[q][v] = fma2(pk(bq[v], bq[v]), ua, accE[q][v]);
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[Q] = 0ull;
                 }
             }
-            // the stage is read: release it and refill it with frame g + S
+            // the stage is read: release it (thread 0 refills it at the next frame)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&freed[s]);
-            if (threadIdx.x == 0 && issued < total_g) {
-                if (!mbar_wait(&freed[s], par, p.wait_cycles)) {
-                    atomicOr(p.err, kErrTimeout);
-                } else {
-                    issue(issued);
-                    ++issued;
-                }
-            }
-            // reduce-scatter over the 32 lanes: lane (l & 3) keeps pair (l & 3)
-            f2 zE[KH], zO[KH];
+            // ---- project (Eqs. 7, 9): lane (q, i) forms coefficients v0 .. v0 + CPL - 1
             {
-                const bool hi = (lane & 2) != 0;
-                f2 rE[2][KH], rO[2][KH];
+                const int q = lane >> 3, v0 = (lane & 7) * CPL;
+                if (v0 < 2 * KH) {
+                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * q + (v0 >= KH)) * Ly.row_bytes);
+                    f2 acc[CPL];
 #pragma unroll
-                for (int pp = 0; pp < 2; ++pp)
+                    for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0ull;
+#pragma unroll 4
+                    for (int r4 = 0; r4 < QP / 4; ++r4) {
+                        const float4 d0 = dat[2 * r4], d1 = dat[2 * r4 + 1];
 #pragma unroll
-                    for (int v = 0; v < KH; ++v) {
-                        float m0, m1, o0, o1;
-                        upk(hi ? accE[pp + 2][v] : accE[pp][v], m0, m1);
-                        upk(hi ? accE[pp][v] : accE[pp + 2][v], o0, o1);
-                        rE[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2), m1 + __shfl_xor_sync(FULLM, o1, 2));
-                        upk(hi ? accO[pp + 2][v] : accO[pp][v], m0, m1);
-                        upk(hi ? accO[pp][v] : accO[pp + 2][v], o0, o1);
-                        rO[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2), m1 + __shfl_xor_sync(FULLM, o1, 2));
+                        for (int cc = 0; cc < CPL; ++cc) {
+                            const float4 w = reinterpret_cast<const float4 *>(basis + (size_t)(v0 + cc) * QP)[r4];
+                            acc[cc] = fma2(pk(w.x, w.x), pk(d0.x, d0.y), acc[cc]);
+                            acc[cc] = fma2(pk(w.y, w.y), pk(d0.z, d0.w), acc[cc]);
+                            acc[cc] = fma2(pk(w.z, w.z), pk(d1.x, d1.y), acc[cc]);
+                            acc[cc] = fma2(pk(w.w, w.w), pk(d1.z, d1.w), acc[cc]);
+                        }
                     }
-                const bool b0 = (lane & 1) != 0;
 #pragma unroll
-                for (int v = 0; v < KH; ++v) {
-                    float m0, m1, o0, o1;
-                    upk(b0 ? rE[1][v] : rE[0][v], m0, m1);
-                    upk(b0 ? rE[0][v] : rE[1][v], o0, o1);
-                    float e0 = m0 + __shfl_xor_sync(FULLM, o0, 1), e1 = m1 + __shfl_xor_sync(FULLM, o1, 1);
-                    upk(b0 ? rO[1][v] : rO[0][v], m0, m1);
-                    upk(b0 ? rO[0][v] : rO[1][v], o0, o1);
-                    float d0 = m0 + __shfl_xor_sync(FULLM, o0, 1), d1 = m1 + __shfl_xor_sync(FULLM, o1, 1);
-#pragma unroll
-                    for (int o = 4; o < 32; o <<= 1) {
-                        e0 += __shfl_xor_sync(FULLM, e0, o);
-                        e1 += __shfl_xor_sync(FULLM, e1, o);
-                        d0 += __shfl_xor_sync(FULLM, d0, o);
-                        d1 += __shfl_xor_sync(FULLM, d1, o);
-                    }
-                    zE[v] = pk(e0, e1);
-                    zO[v] = pk(d0, d1);
+                    for (int cc = 0; cc < CPL; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + v0 + cc] = acc[cc];
                 }
             }
-            // lag grid: the 8 lanes holding a pair split the steps m = gi, gi + 8, ...
+            __syncwarp();
+            // ---- lag grid: the 8 lanes holding a pair split the steps m = gi, gi + 8, ...
             const int q = lane & 3, gi = lane >> 2;
+            // the coefficients are read from the warp's buffer where used (the R state holds the registers)
+            const f2 *zE = reinterpret_cast<const f2 *>(zbuf) + q * 2 * KH, *zO = zE + KH;
             const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
             float best = -FLT_MAX;
             int bi = 0x7fffffff;
@@ -444,11 +460,8 @@ fcc_status_t smooth_geometry(const fcc_plan *plan, long long T, SmoothPlan &g)
     g.chunk = (int)std::max<long long>(64, (T + target - 1) / target);
     g.n_chunks = (int)((T + g.chunk - 1) / g.chunk);
     g.threads = 32 * plan->n_slots;
-    const int frame_bytes = in.M * in.B * 8;
-    const size_t stage = ((size_t)frame_bytes + 127) & ~(size_t)127;
-    const size_t tabs = (128 + 8 * sizeof(Slot) + (size_t)((in.Q + 1) * 2 * plan->kh + (in.center + 1) * 4 * plan->kh) * 4 +
-                         127) & ~(size_t)127;
-    g.smem = tabs + kSmoothStages * stage;
+    const SmoothLayout Ly(in.Q, plan->kh, in.center, in.M, in.B, plan->n_slots);
+    g.smem = Ly.total;
     g.work_bytes = (size_t)g.n_chunks * in.P * in.B * sizeof(float2);
     return FCC_OK;
 }
@@ -539,15 +552,16 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "smoothing carry kernels");
     }
-    // basis in the smoothed kernel's layout: row f = (even weights, odd weights)
+    // basis in the smoothed kernel's layout: row v < KH = even basis v over
+    // records 0..Q, row KH + v = odd basis v (zero at Q); padding records zero
     if (!plan->d_smooth_basis) {
         const int kh = plan->kh, Q = in.Q;
-        std::vector<float> bas((size_t)(Q + 1) * 2 * kh, 0.f);
-        for (int f = 0; f <= Q; ++f) {
-            for (int k = 0; k < in.K_even; ++k) bas[(size_t)f * 2 * kh + k] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
-            if (f < Q)
-                for (int k = 0; k < in.K_odd; ++k) bas[(size_t)f * 2 * kh + kh + k] = (float)plan->Po[(size_t)k * Q + f];
-        }
+        const SmoothLayout Ly(Q, kh, in.center, in.M, in.B, plan->n_slots);
+        std::vector<float> bas((size_t)2 * kh * Ly.QP, 0.f);
+        for (int k = 0; k < in.K_even; ++k)
+            for (int f = 0; f <= Q; ++f) bas[(size_t)k * Ly.QP + f] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
+        for (int k = 0; k < in.K_odd; ++k)
+            for (int f = 0; f < Q; ++f) bas[(size_t)(kh + k) * Ly.QP + f] = (float)plan->Po[(size_t)k * Q + f];
         float *d = nullptr;
         FCC_CUDA_TRY(cudaMalloc(&d, bas.size() * sizeof(float)));
         FCC_CUDA_TRY(cudaMemcpy(d, bas.data(), bas.size() * sizeof(float), cudaMemcpyHostToDevice));

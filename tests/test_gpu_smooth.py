@@ -99,6 +99,20 @@ def test_stream_continues_across_calls(B, O):
     plan.close()
 
 
+@pytest.mark.parametrize("scale", [1e-17, 1e17])
+def test_extreme_magnitudes(B, O, scale):
+    # |R|^2 underflows (1e-17) or overflows (1e17) FP32 although R itself is a
+    # normal number: the phase transform must rescale rather than lose R_hat
+    X = (_spectra(90, 4, 256, seed=21).astype(np.complex128) * scale).astype(np.complex64)
+    plan = B.Plan(4, 16000.0, 256, 4, tau_max=3)
+    out = plan.tdoa_smoothed(torch.from_numpy(X).cuda(), 0.1)
+    plan.sync()
+    basis = O.Basis(256, 3, 4, K=plan.K)
+    ref = O.tdoa_smoothed(X, basis.WK, basis.taus, basis.delta, 0.1, want_y=True)
+    _check(out, ref)
+    plan.close()
+
+
 def test_zero_bins_nan_and_arguments(B):
     plan = B.Plan(4, 16000.0, 256, 4, tau_max=3)
     X = _spectra(80, 4, 256, seed=9, zero_frac=0.3)  # zero cross-spectra where a mic bin is 0
