@@ -518,3 +518,70 @@ void or_adam(double *p, const double *g, double *m, double *v, long long n, int 
         p[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
     }
 }
+
+/*
+ * Multi-pair DoA search over direction candidates (the step the paper's
+ * conclusion names after per-pair TDoA; the paper prints no formula, so this
+ * is the steered-response power it refers to): for a candidate unit vector u,
+ * a far-field plane wave from u reaches mic m at t_m = -(fs / c) (r_m . u)
+ * samples, so pair (i, j) sees tau_ij(u) = t_i - t_j.  The pair's correlation
+ * on the lag grid y_ij(tau_k), tau_k = -L + k / den, is read at tau_ij(u) by
+ * linear interpolation (grid position (tau + L) den, clamped to [0, I - 1]);
+ * score(u) = sum over pairs.  Per frame: the best candidate (lowest index on
+ * an exact tie) and its score; scores_out (may be NULL) gets every score.
+ *
+ * y: [T][P][I] (pairs i < j lexicographic); mic_xyz: [M][3] metres;
+ * dirs: [D][3] unit vectors.  Frames in parallel.
+ */
+void or_doa_srp(const double *y, long long T, int M, int I, int L, int den, const double *mic_xyz,
+                double fs, double c, const double *dirs, int D, int *idx_out, double *score_out,
+                double *scores_out, int n_threads)
+{
+    int P = M * (M - 1) / 2;
+    /* grid positions and weights per (direction, pair), FP64 */
+    int *k0 = (int *)malloc(sizeof(int) * (size_t)D * P);
+    double *wt = (double *)malloc(sizeof(double) * (size_t)D * P);
+    for (int d = 0; d < D; ++d) {
+        int p = 0;
+        for (int i = 0; i < M; ++i)
+            for (int j = i + 1; j < M; ++j, ++p) {
+                double ti = -(fs / c) * (mic_xyz[3 * i] * dirs[3 * d] + mic_xyz[3 * i + 1] * dirs[3 * d + 1] +
+                                         mic_xyz[3 * i + 2] * dirs[3 * d + 2]);
+                double tj = -(fs / c) * (mic_xyz[3 * j] * dirs[3 * d] + mic_xyz[3 * j + 1] * dirs[3 * d + 1] +
+                                         mic_xyz[3 * j + 2] * dirs[3 * d + 2]);
+                double pos = (ti - tj + (double)L) * (double)den;
+                if (pos < 0.0) pos = 0.0;
+                if (pos > (double)(I - 1)) pos = (double)(I - 1);
+                int k = (int)floor(pos);
+                if (k > I - 2) k = I - 2;
+                k0[(size_t)d * P + p] = k;
+                wt[(size_t)d * P + p] = pos - (double)k;
+            }
+    }
+#ifdef _OPENMP
+    if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for num_threads(n_threads) schedule(static)
+#endif
+    for (long long t = 0; t < T; ++t) {
+        const double *yt = y + (size_t)t * P * I;
+        int best = 0;
+        double best_s = 0.0;
+        for (int d = 0; d < D; ++d) {
+            double s = 0.0;
+            for (int p = 0; p < P; ++p) {
+                int k = k0[(size_t)d * P + p];
+                double w = wt[(size_t)d * P + p];
+                s += (1.0 - w) * yt[(size_t)p * I + k] + w * yt[(size_t)p * I + k + 1];
+            }
+            if (scores_out) scores_out[(size_t)t * D + d] = s;
+            if (d == 0 || s > best_s) {
+                best = d;
+                best_s = s;
+            }
+        }
+        idx_out[t] = best;
+        score_out[t] = best_s;
+    }
+    free(k0);
+    free(wt);
+}

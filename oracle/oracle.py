@@ -14,6 +14,9 @@ follows the paper's definitions literally in FP64:
   rank K (W_K); K from the energy rule when not given.
 * Sec. 2 (eq. 1, alpha = 1) -- R_hat = X_i X_j^* / |X_i X_j^*|.
 * Eq. 2 / Eq. 4 -- y = 2 Re{W_K x}; argmax; three-point quadratic refinement.
+* Conclusion (next step: a DoA search over candidates using every pair's
+  TDoA) -- steered-response power over unit-vector candidates from the
+  pairs' correlations on the lag grid (``doa_srp``).
 """
 from __future__ import annotations
 
@@ -90,6 +93,10 @@ def _load():
             lib.or_adam.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.or_adam.restype = None
+            lib.or_doa_srp.argtypes = [_dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       _dp, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int, _ip, _dp, _dp,
+                                       ctypes.c_int]
+            lib.or_doa_srp.restype = None
             lib.or_max_threads.argtypes = []
             lib.or_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -234,6 +241,31 @@ def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: b
                     idx.ctypes.data_as(_ip), _d(peak), _d(tau),
                     _d(y) if want_y else None, nt)
     return idx, peak, tau, y
+
+
+def doa_srp(y: np.ndarray, L: int, den: int, mic_xyz: np.ndarray, fs: float, c: float, dirs: np.ndarray,
+            want_scores: bool = False, threads: int | None = None):
+    """DoA search over candidate directions (the next step named in the paper's
+    conclusion; it prints no formula): score(u) = sum over pairs i < j of the
+    pair's correlation y_ij read at tau_ij(u) = -(fs/c)(r_i - r_j).u samples by
+    linear interpolation on the lag grid tau_k = -L + k/den (clamped to the
+    grid's ends).  y: [T, P, I]; mic_xyz: [M, 3] metres; dirs: [D, 3] unit
+    vectors.  Returns (best index [T] int32, best score [T], scores [T, D] or
+    None); the lowest index wins an exact tie."""
+    y = np.ascontiguousarray(y, np.float64)
+    T, P, I = y.shape
+    xyz = np.ascontiguousarray(mic_xyz, np.float64)
+    M = xyz.shape[0]
+    assert P == M * (M - 1) // 2 and I == 2 * L * den + 1
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    D = dirs.shape[0]
+    idx = np.empty(T, np.int32)
+    score = np.empty(T)
+    scores = np.empty((T, D)) if want_scores else None
+    nt = max_threads() if threads is None else int(threads)
+    _load().or_doa_srp(_d(y), T, M, I, L, den, _d(xyz), float(fs), float(c), _d(dirs), D, idx.ctypes.data_as(_ip),
+                       _d(score), _d(scores) if want_scores else None, nt)
+    return idx, score, scores
 
 
 # ----------------------------------------------------------------------------

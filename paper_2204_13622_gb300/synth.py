@@ -68,6 +68,17 @@ def unit_vector(azimuth: float, elevation: float = 0.0) -> np.ndarray:
                      math.cos(elevation) * math.sin(azimuth), math.sin(elevation)])
 
 
+def fibonacci_directions(n: int, hemisphere: bool = True) -> np.ndarray:
+    """n quasi-uniform unit vectors on the sphere (Fibonacci lattice), [n, 3];
+    z in (0, 1) for the upper hemisphere (enough for a planar array, whose
+    delays cannot tell z from -z), else in (-1, 1)."""
+    k = np.arange(n) + 0.5
+    z = 1.0 - k / n if hemisphere else 1.0 - 2.0 * k / n
+    phi = math.pi * (1.0 + math.sqrt(5.0)) * k
+    r = np.sqrt(1.0 - z * z)
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
 def far_field_delays(xyz: np.ndarray, direction: np.ndarray, fs: float,
                      c: float = SPEED_OF_SOUND) -> np.ndarray:
     """Per-mic delay (samples) of a far-field source from `direction`."""
