@@ -388,6 +388,22 @@ def smooth_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float
     return (6 * B + 12 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (4 * (KE + KO) + 2))
 
 
+SMEM_PEAK_BPS = 152 * 128 * 2.070e9  # shared memory: 128 bytes per clock per SM
+
+
+def smem_roofline(nbytes: float, ms: float, kernel: str, alu=None) -> dict:
+    """A kernel bound by shared-memory bandwidth: `nbytes` the algorithmic bytes
+    read from shared memory per launch (8 per candidate, pair and frame for the
+    DoA search: the interpolation pair (y_k, y_{k+1} - y_k))."""
+    achieved = nbytes / (ms / 1000.0)
+    r = {"bound": "smem", "achieved": achieved / 1e9, "peak": SMEM_PEAK_BPS / 1e9, "unit": "GB/s",
+         "frac": achieved / SMEM_PEAK_BPS, "kernel": kernel, "bytes_per_launch": nbytes, "traffic": None,
+         "peak_source": "152 SMs x 128 B/clock x 2070 MHz"}
+    if alu is not None:
+        r["alu"] = {k: alu[k] for k in ("achieved", "peak", "unit", "frac")}
+    return r
+
+
 def alu_roofline(ops: float, ms: float, kernel: str) -> dict:
     achieved = ops / (ms / 1000.0)
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_OPS / 1e12, "unit": "TFLOP/s",
@@ -486,6 +502,100 @@ def run_batched(args, rank, world, local):
                "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
     batch.close()
     return res
+
+
+def run_doa(args, rank, world, local):
+    """DoA search (the step after per-pair TDoA named in the paper's conclusion):
+    spectra in, per frame the best of D candidate directions out, through
+    fcc_tdoa_doa (FCC with the lag-grid correlations, chunk by chunk, then the
+    search); also times FCC with the correlation output and the search alone."""
+    import numpy as np
+    import torch
+
+    from paper_2204_13622_gb300 import binding, synth, workloads
+    w = workloads.CIRCLE8
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    distributed = dist_init(world, "nccl")
+    T, P = (args.frames or w.T), w.P
+    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, mic_xyz=w.xyz, device=local)
+    dirs = synth.fibonacci_directions(args.dirs)
+    doa = binding.Doa(plan, w.xyz, dirs)
+    work = torch.empty(doa.workspace(T), dtype=torch.uint8, device=dev)
+    out = doa.tdoa_doa(X, work=work)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        doa.tdoa_doa(X, work=work, out=out)
+    plan.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(distributed)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            doa.tdoa_doa(X, work=work, out=out)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(distributed)
+    plan.sync()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = sum(per) / args.steps
+    ms_max = max_over_ranks(ms, distributed, dev)
+    res = None
+    if rank == 0:
+        # the two stages alone: FCC with the correlation output, the search over it
+        n = min(T, 1 << 18)
+        o = plan.tdoa(X[:n], tau_hat=False, corr=True)
+        s_out = doa.search(o["corr"])
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _ in range(2):
+            e[0].record(stream)
+            plan.tdoa(X[:n], tau_hat=False, corr=True, out=o)
+            e[1].record(stream)
+            doa.search(o["corr"], out=s_out)
+            e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        fcc_ms, srp_ms = e[0].elapsed_time(e[1]) * T / n, e[1].elapsed_time(e[2]) * T / n
+        # accuracy: 64 sampled frames against the oracle's FP64 correlations and search
+        from oracle import oracle as O
+        sel = np.linspace(0, T - 1, 64).astype(np.int64)
+        basis = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+        t1 = time.perf_counter()
+        _, _, _, y = O.tdoa(X[sel].cpu().numpy(), basis.WK, basis.taus, basis.delta, want_y=True)
+        ref_idx, _, scores = O.doa_srp(y, w.L, w.lag_den, w.xyz, w.fs, 343.0, dirs, want_scores=True)
+        t_or = time.perf_counter() - t1
+        got = out["dir_idx"][torch.from_numpy(sel).to(dev)].cpu().numpy()
+        srp_ops = 2.0 * args.dirs * P * T  # one FMA and one add per (candidate, pair, frame)
+        res = {"metric": METRIC, "value": whole_job_rate(T * P, world, ms_max / 1000.0), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"{w.name}, DoA search over {args.dirs} hemisphere candidates",
+                          "frames": T, "pairs": P, "candidates": args.dirs,
+                          "l2": "inputs larger than L2; no flush"},
+               "frames_per_s": T / (ms_max / 1000.0),
+               "stages_ms": {"fcc_with_corr": fcc_ms, "search": srp_ms},
+               "roofline": smem_roofline(8.0 * args.dirs * P * T, srp_ms, "srp_kernel (the search alone)",
+                                         alu=alu_roofline(srp_ops, srp_ms, "srp_kernel")),
+               "accuracy_vs_oracle": {"frames": int(len(sel)),
+                                      "dir_agreement": float((got == ref_idx).mean()),
+                                      "score_loss_max": float((scores[np.arange(len(sel)), ref_idx]
+                                                               - scores[np.arange(len(sel)), got]).max())},
+               "cpu_baseline": {"value": len(sel) * P / t_or, "unit": UNIT, "cores": O.max_threads(),
+                                "kind": "oracle", "sample": "64 frames: FP64 FCC correlations + FP64 search"},
+               "gpu_launches": 2 * args.steps * ((T + doa_chunk(doa, T) - 1) // doa_chunk(doa, T)),
+               "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
+    doa.close()
+    plan.close()
+    return res
+
+
+def doa_chunk(doa, T):
+    """Frames per chunk of fcc_tdoa_doa (its workspace holds one chunk's
+    correlations, lag indices and peaks: P (I + 2) 4 bytes per frame)."""
+    p = doa.plan
+    return max(1, min(T, doa.workspace(T) // (p.P * (p.I + 2) * 4)))
 
 
 def run_smoothed(args, rank, world, local):
@@ -647,11 +757,12 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
     ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
     ap.add_argument("--workload", default="circle8",
-                    choices=["circle8", "grid16", "square4", "batched", "learned"])
+                    choices=["circle8", "grid16", "square4", "batched", "learned", "doa"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="Eq. 1 smoothing factor; < 1 times the smoothed path (FCC leg only)")
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
+    ap.add_argument("--dirs", type=int, default=1024, help="doa: candidate directions (hemisphere)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batched: keep the heuristic tile shapes (default: autotuned)")
     ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")
@@ -670,6 +781,8 @@ def main(argv=None):
             res = run_batched(args, rank, world, local)
         elif args.workload == "learned":
             res = run_learned(args, rank, world, local) if rank == 0 else None
+        elif args.workload == "doa":
+            res = run_doa(args, rank, world, local)
         else:
             res = run_fcc(args, rank, world, local)
     if res is not None:

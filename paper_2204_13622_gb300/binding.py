@@ -35,7 +35,9 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            # include/fcc_debug.h
            "fcc_debug_set",
            # include/fcc_smooth.h
-           "fcc_smooth_workspace", "fcc_tdoa_smoothed"]
+           "fcc_smooth_workspace", "fcc_tdoa_smoothed",
+           # include/fcc_doa.h
+           "fcc_doa_create", "fcc_doa_destroy", "fcc_doa_search", "fcc_doa_workspace", "fcc_tdoa_doa"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -145,6 +147,14 @@ def lib():
                                         _vp, _vp, _vp, _vp, _vp]
         L.fcc_tdoa_smoothed.restype = ctypes.c_int
         L.fcc_batch_sync.argtypes = [_vp, _vp]
+        L.fcc_doa_create.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.fcc_doa_destroy.argtypes = [_vp]
+        L.fcc_doa_destroy.restype = None
+        L.fcc_doa_search.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp]
+        L.fcc_doa_workspace.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.fcc_tdoa_doa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp]
+        for name in ("fcc_doa_create", "fcc_doa_search", "fcc_doa_workspace", "fcc_tdoa_doa"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_plan_geometry", "fcc_plan_autotune", "fcc_batch_create", "fcc_batch_info",
                      "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):
             getattr(L, name).restype = ctypes.c_int
@@ -361,6 +371,76 @@ class Plan:
         check(lib().fcc_plan_autotune(self._h, cache_path.encode() if cache_path else None, int(force),
                                       int(max_candidates), ctypes.byref(us)), "fcc_plan_autotune")
         return us.value
+
+
+class Doa:
+    """include/fcc_doa.h: the search over candidate directions (unit vectors
+    `dirs` [D, 3]) from the pairs' correlations on `plan`'s lag grid; `mic_xyz`
+    [M, 3] metres.  The plan must stay open while this object is used."""
+
+    def __init__(self, plan: Plan, mic_xyz, dirs):
+        xyz = np.ascontiguousarray(mic_xyz, np.float64)
+        d = np.ascontiguousarray(dirs, np.float64)
+        if xyz.shape != (plan.M, 3) or d.ndim != 2 or d.shape[1] != 3:
+            raise ValueError(f"mic_xyz must be [{plan.M}, 3] and dirs [D, 3]")
+        h = _vp()
+        check(lib().fcc_doa_create(plan._h, xyz.ctypes.data_as(_dp), d.ctypes.data_as(_dp), d.shape[0],
+                                   ctypes.byref(h)), "fcc_doa_create")
+        self._h, self.plan, self.D = h, plan, d.shape[0]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fcc_doa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, T: int) -> int:
+        b = ctypes.c_longlong()
+        check(lib().fcc_doa_workspace(self._h, int(T), ctypes.byref(b)), "fcc_doa_workspace")
+        return b.value
+
+    def _out(self, T, dev, out):
+        import torch
+        if out is None:
+            out = {"dir_idx": torch.empty(T, dtype=torch.int32, device=dev),
+                   "score": torch.empty(T, dtype=torch.float32, device=dev)}
+        return out
+
+    def search(self, corr, stream=None, out=None):
+        """fcc_doa_search over correlations corr float32 [T, P, I] on the device."""
+        import torch
+        p = self.plan
+        if corr.dtype != torch.float32 or corr.dim() != 3 or tuple(corr.shape[1:]) != (p.P, p.I) \
+                or not corr.is_contiguous():
+            raise ValueError(f"corr must be contiguous float32 [T, {p.P}, {p.I}]")
+        T, dev = corr.shape[0], corr.device
+        out = self._out(T, dev, out)
+        check(lib().fcc_doa_search(self._h, _ptr(corr), T, _ptr(out["dir_idx"]), _ptr(out["score"]),
+                                   _stream(stream, dev)), "fcc_doa_search")
+        return out
+
+    def tdoa_doa(self, X, pairs: bool = False, work=None, stream=None, out=None):
+        """fcc_tdoa_doa: spectra X complex64 [T, M, B] in, per-frame candidate
+        index and score out (and, with pairs=True, the per-pair lag_idx / peak)."""
+        import torch
+        p = self.plan
+        p._check_spectra(X)
+        T, dev = X.shape[0], X.device
+        if work is None:
+            work = torch.empty(max(self.workspace(T), 16), dtype=torch.uint8, device=dev)
+        out = self._out(T, dev, out)
+        if pairs and "lag_idx" not in out:
+            out["lag_idx"] = torch.empty((T, p.P), dtype=torch.int32, device=dev)
+            out["peak"] = torch.empty((T, p.P), dtype=torch.float32, device=dev)
+        check(lib().fcc_tdoa_doa(self._h, _ptr(X), T, _ptr(out["dir_idx"]), _ptr(out["score"]),
+                                 _ptr(out.get("lag_idx")), _ptr(out.get("peak")), _ptr(work), work.numel(),
+                                 _stream(stream, dev)), "fcc_tdoa_doa")
+        return out
 
 
 def plan_bases_noalloc(n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0, mic_xyz=None,

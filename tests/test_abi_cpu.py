@@ -57,6 +57,12 @@ def test_null_arguments_rejected_without_gpu(lib):
     d = binding.PlanDesc(4, None, 16000.0, 500, 343.0, 3.0, 4, 0, 0.999, 0, 0)
     assert lib.fcc_plan_create(ctypes.byref(d), ctypes.byref(h)) == 1  # N not a power of two
     assert "power of two" in lib.fcc_last_error().decode()
+    # DoA search entry points
+    assert lib.fcc_doa_create(None, None, None, 4, ctypes.byref(h)) == 1 and not h.value
+    assert lib.fcc_doa_search(None, None, 0, None, None, None) == 1
+    assert lib.fcc_doa_workspace(None, 10, None) == 1
+    assert lib.fcc_tdoa_doa(None, None, 0, None, None, None, None, None, 0, None) == 1
+    lib.fcc_doa_destroy(None)  # no-op
 
 
 def test_debug_hooks_validate_arguments(lib):
