@@ -14,6 +14,8 @@ follows the paper's definitions literally in FP64:
   rank K (W_K); K from the energy rule when not given.
 * Sec. 2 (eq. 1, alpha = 1) -- R_hat = X_i X_j^* / |X_i X_j^*|.
 * Eq. 2 / Eq. 4 -- y = 2 Re{W_K x}; argmax; three-point quadratic refinement.
+* Sec. 2 -- the STFT X(t, f) of the microphone signals (``stft``): periodic
+  Hann window, frames of N samples every hop samples, no padding.
 * Conclusion (next step: a DoA search over candidates using every pair's
   TDoA) -- steered-response power over unit-vector candidates from the
   pairs' correlations on the lag grid (``doa_srp``).
@@ -241,6 +243,27 @@ def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: b
                     idx.ctypes.data_as(_ip), _d(peak), _d(tau),
                     _d(y) if want_y else None, nt)
     return idx, peak, tau, y
+
+
+def stft(pcm: np.ndarray, N: int, hop: int) -> np.ndarray:
+    """The STFT the method starts from (Sec. 2: X_m(t, f) of each microphone
+    signal; the window and framing are not printed, so: periodic Hann window
+    w[n] = 0.5 - 0.5 cos(2 pi n / N), frame t = samples t hop .. t hop + N - 1,
+    no padding, T = 1 + (n_samples - N) // hop frames, 0 if n_samples < N).
+    pcm: interleaved [n_samples, M], float (used as is) or int16 (divided by
+    32768).  Returns X [T, M, N/2 + 1] complex128 with X[t, m, k] =
+    sum_n w[n] x[t hop + n, m] exp(-j 2 pi k n / N) (numpy's rfft is the DFT)."""
+    x = np.asarray(pcm)
+    x = x.astype(np.float64) / 32768.0 if x.dtype == np.int16 else x.astype(np.float64)
+    n_samples, M = x.shape
+    T = 0 if n_samples < N else 1 + (n_samples - N) // hop
+    n = np.arange(N)
+    w = 0.5 - 0.5 * np.cos(2.0 * np.pi * n / N)
+    X = np.empty((T, M, N // 2 + 1), np.complex128)
+    for t in range(T):
+        frame = x[t * hop:t * hop + N, :] * w[:, None]  # [N, M]
+        X[t] = np.fft.rfft(frame, axis=0).T
+    return X
 
 
 def doa_srp(y: np.ndarray, L: int, den: int, mic_xyz: np.ndarray, fs: float, c: float, dirs: np.ndarray,
