@@ -504,6 +504,109 @@ def run_batched(args, rank, world, local):
     return res
 
 
+def run_pcm(args, rank, world, local):
+    """STFT front-end: interleaved int16 PCM of the 8-mic circle in, per-pair
+    TDoA out (fcc_tdoa_pcm: STFT and FCC chunk by chunk, the spectra kept in
+    L2-sized chunks); e2e through fcc_tdoa_pcm_host from pinned host PCM."""
+    import numpy as np
+    import torch
+
+    from paper_2204_13622_gb300 import binding, synth, workloads
+    w = workloads.CIRCLE8
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    distributed = dist_init(world, "nccl")
+    T, P, hop = (args.frames or w.T), w.P, w.hop
+    n = (T - 1) * hop + w.N
+    pcm = synth.pcm_far_field(n, w.xyz, w.fs, seed=rank_seed(rank), device=dev)
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, mic_xyz=w.xyz, device=local)
+    work = torch.empty(plan.pcm_workspace(n, hop), dtype=torch.uint8, device=dev)
+    out = plan.tdoa_pcm(pcm, hop, work=work)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        plan.tdoa_pcm(pcm, hop, work=work, out=out)
+    plan.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(distributed)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            plan.tdoa_pcm(pcm, hop, work=work, out=out)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(distributed)
+    plan.sync()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = sum(per) / args.steps
+    ms_max = max_over_ranks(ms, distributed, dev)
+    res = None
+    if rank == 0:
+        # the stages alone over 2^18 frames: STFT to HBM, FCC from HBM
+        nf = min(T, 1 << 18)
+        sub = pcm[:(nf - 1) * hop + w.N]
+        X = plan.stft(sub, hop)
+        o = plan.tdoa(X)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _ in range(2):
+            e[0].record(stream)
+            plan.stft(sub, hop, out=X)
+            e[1].record(stream)
+            plan.tdoa(X, out=o)
+            e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        stft_ms, fcc_ms = e[0].elapsed_time(e[1]) * T / nf, e[1].elapsed_time(e[2]) * T / nf
+        del X, o
+        # e2e: pinned host PCM in, host results out
+        host = pcm.cpu().pin_memory()
+        hout = plan.tdoa_pcm_host(host, hop)
+        t1 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            plan.tdoa_pcm_host(host, hop, out=hout)
+        e2e_s = (time.perf_counter() - t1) / reps
+        h2d = host.numel() * host.element_size()
+        d2h = T * P * 12
+        # accuracy: 64 sampled frames through the FP64 chain (oracle STFT + FCC)
+        from oracle import oracle as O
+        sel = np.linspace(0, T - 1, 64).astype(np.int64)
+        seg = torch.cat([pcm[t * hop:t * hop + w.N] for t in sel]).cpu().numpy()
+        basis = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+        t2 = time.perf_counter()
+        Xo = O.stft(seg, w.N, w.N).astype(np.complex64)
+        idx, _, _, y = O.tdoa(Xo, basis.WK, basis.taus, basis.delta, want_y=True)
+        t_or = time.perf_counter() - t2
+        got = out["lag_idx"][torch.from_numpy(sel).to(dev)].cpu().numpy()
+        srt = np.sort(y, axis=-1)
+        clear = (srt[..., -1] - srt[..., -2]) > 4e-6 * np.abs(y).max(-1)
+        H = w.N // 2
+        import math as _m
+        p4 = int(round(_m.log(H, 4) - 0.5))  # radix-4 passes
+        r2 = 1 if 4 ** p4 < H else 0
+        stft_ops = w.M * T * (p4 * (H // 4) * 28 + r2 * (H // 2) * 8 + (H + 1) * 14 + 2 * w.N)
+        res = {"metric": METRIC, "value": whole_job_rate(T * P, world, ms_max / 1000.0), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"{w.name}, int16 PCM in (hop {hop}) through the STFT front-end",
+                          "frames": T, "pairs": P, "pcm_bytes": h2d, "l2": "inputs larger than L2; no flush"},
+               "stages_ms": {"stft_to_hbm": stft_ms, "fcc_from_hbm": fcc_ms},
+               "e2e": {"value": T * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": e2e_s * 1000.0, "path": "fcc_tdoa_pcm_host, pinned host PCM"},
+               "roofline": dict(alu_roofline(stft_ops, stft_ms, "stft_kernel (alone, spectra to HBM)"),
+                                traffic=None, hbm_write_gb=T * w.M * w.B * 8 / 1e9),
+               "accuracy_vs_oracle": {"pair_frames": int(got.size),
+                                      "argmax_agreement_clear": float((got == idx)[clear].mean()),
+                                      "argmax_agreement": float((got == idx).mean())},
+               "cpu_baseline": {"value": len(sel) * P / t_or, "unit": UNIT, "cores": O.max_threads(),
+                                "kind": "oracle", "sample": "64 frames: FP64 STFT + FP64 FCC"},
+               "gpu_launches": 2 * args.steps * ((T + plan.pcm_workspace(n, hop) // (w.M * w.B * 8) - 1)
+                                                 // (plan.pcm_workspace(n, hop) // (w.M * w.B * 8))),
+               "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
+    plan.close()
+    return res
+
+
 def run_doa(args, rank, world, local):
     """DoA search (the step after per-pair TDoA named in the paper's conclusion):
     spectra in, per frame the best of D candidate directions out, through
@@ -757,7 +860,7 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
     ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
     ap.add_argument("--workload", default="circle8",
-                    choices=["circle8", "grid16", "square4", "batched", "learned", "doa"])
+                    choices=["circle8", "grid16", "square4", "batched", "learned", "doa", "pcm"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="Eq. 1 smoothing factor; < 1 times the smoothed path (FCC leg only)")
@@ -783,6 +886,8 @@ def main(argv=None):
             res = run_learned(args, rank, world, local) if rank == 0 else None
         elif args.workload == "doa":
             res = run_doa(args, rank, world, local)
+        elif args.workload == "pcm":
+            res = run_pcm(args, rank, world, local)
         else:
             res = run_fcc(args, rank, world, local)
     if res is not None:

@@ -37,7 +37,10 @@ EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_tau
            # include/fcc_smooth.h
            "fcc_smooth_workspace", "fcc_tdoa_smoothed",
            # include/fcc_doa.h
-           "fcc_doa_create", "fcc_doa_destroy", "fcc_doa_search", "fcc_doa_workspace", "fcc_tdoa_doa"]
+           "fcc_doa_create", "fcc_doa_destroy", "fcc_doa_search", "fcc_doa_workspace", "fcc_tdoa_doa",
+           # include/fcc_stft.h
+           "fcc_stft_frames", "fcc_stft", "fcc_pcm_workspace", "fcc_tdoa_pcm", "fcc_tdoa_pcm_host"]
+PCM = {"f32": 0, "s16": 1}
 
 
 class PlanDesc(ctypes.Structure):
@@ -154,6 +157,14 @@ def lib():
         L.fcc_doa_workspace.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
         L.fcc_tdoa_doa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp]
         for name in ("fcc_doa_create", "fcc_doa_search", "fcc_doa_workspace", "fcc_tdoa_doa"):
+            getattr(L, name).restype = ctypes.c_int
+        _ll, _i = ctypes.c_longlong, ctypes.c_int
+        L.fcc_stft_frames.argtypes = [_vp, _ll, _i, ctypes.POINTER(_ll)]
+        L.fcc_stft.argtypes = [_vp, _vp, _i, _ll, _i, _vp, _vp]
+        L.fcc_pcm_workspace.argtypes = [_vp, _ll, _i, ctypes.POINTER(_ll)]
+        L.fcc_tdoa_pcm.argtypes = [_vp, _vp, _i, _ll, _i, _vp, _vp, _vp, _vp, _ll, _vp]
+        L.fcc_tdoa_pcm_host.argtypes = [_vp, _vp, _i, _ll, _i, _vp, _vp, _vp, _vp]
+        for name in ("fcc_stft_frames", "fcc_stft", "fcc_pcm_workspace", "fcc_tdoa_pcm", "fcc_tdoa_pcm_host"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("fcc_plan_geometry", "fcc_plan_autotune", "fcc_batch_create", "fcc_batch_info",
                      "fcc_batch_array_info", "fcc_batch_bind", "fcc_batch_run", "fcc_batch_sync"):
@@ -357,6 +368,71 @@ class Plan:
         check(lib().fcc_tdoa_smoothed(self._h, _ptr(X), T, float(alpha), _ptr(state), _ptr(work), work.numel(),
                                       _ptr(out["lag_idx"]), _ptr(out["peak"]), _ptr(out.get("tau_hat")),
                                       _ptr(out.get("coeffs")), _stream(stream, dev)), "fcc_tdoa_smoothed")
+        return out
+
+    # ---- STFT front-end (include/fcc_stft.h)
+    def _pcm_type(self, pcm):
+        import torch
+        kinds = {torch.float32: PCM["f32"], torch.int16: PCM["s16"]}
+        if pcm.dtype not in kinds or pcm.dim() != 2 or pcm.shape[1] != self.M or not pcm.is_contiguous():
+            raise ValueError(f"PCM must be contiguous float32 or int16 [n_samples, {self.M}]")
+        return kinds[pcm.dtype]
+
+    def stft_frames(self, n_samples: int, hop: int) -> int:
+        T = ctypes.c_longlong()
+        check(lib().fcc_stft_frames(self._h, int(n_samples), int(hop), ctypes.byref(T)), "fcc_stft_frames")
+        return T.value
+
+    def stft(self, pcm, hop: int, stream=None, out=None):
+        """fcc_stft: device PCM [n_samples, M] -> spectra complex64 [T, M, N/2+1]."""
+        import torch
+        kind = self._pcm_type(pcm)
+        T, dev = self.stft_frames(pcm.shape[0], hop), pcm.device
+        if out is None:
+            out = torch.empty((T, self.M, self.B), dtype=torch.complex64, device=dev)
+        check(lib().fcc_stft(self._h, _ptr(pcm), kind, pcm.shape[0], int(hop), _ptr(out), _stream(stream, dev)),
+              "fcc_stft")
+        return out
+
+    def pcm_workspace(self, n_samples: int, hop: int) -> int:
+        b = ctypes.c_longlong()
+        check(lib().fcc_pcm_workspace(self._h, int(n_samples), int(hop), ctypes.byref(b)), "fcc_pcm_workspace")
+        return b.value
+
+    def tdoa_pcm(self, pcm, hop: int, tau_hat: bool = True, work=None, stream=None, out=None):
+        """fcc_tdoa_pcm: device PCM in, per-pair TDoA out (the spectra stay on chip in chunks)."""
+        import torch
+        kind = self._pcm_type(pcm)
+        T, dev = self.stft_frames(pcm.shape[0], hop), pcm.device
+        if work is None:
+            work = torch.empty(max(self.pcm_workspace(pcm.shape[0], hop), 16), dtype=torch.uint8, device=dev)
+        if out is None:
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, device=dev),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, device=dev)}
+            if tau_hat:
+                out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, device=dev)
+        check(lib().fcc_tdoa_pcm(self._h, _ptr(pcm), kind, pcm.shape[0], int(hop), _ptr(out["lag_idx"]),
+                                 _ptr(out["peak"]), _ptr(out.get("tau_hat")), _ptr(work), work.numel(),
+                                 _stream(stream, dev)), "fcc_tdoa_pcm")
+        return out
+
+    def tdoa_pcm_host(self, pcm, hop: int, tau_hat: bool = True, stream=None, out=None):
+        """fcc_tdoa_pcm_host: host PCM (a CPU tensor; pinned for full link speed)
+        in, host results out; synchronous."""
+        import torch
+        kind = self._pcm_type(pcm)
+        if pcm.device.type != "cpu":
+            raise ValueError("tdoa_pcm_host takes host PCM")
+        T = self.stft_frames(pcm.shape[0], hop)
+        if out is None:
+            pin = pcm.is_pinned()
+            out = {"lag_idx": torch.empty((T, self.P), dtype=torch.int32, pin_memory=pin),
+                   "peak": torch.empty((T, self.P), dtype=torch.float32, pin_memory=pin)}
+            if tau_hat:
+                out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, pin_memory=pin)
+        check(lib().fcc_tdoa_pcm_host(self._h, _ptr(pcm), kind, pcm.shape[0], int(hop), _ptr(out["lag_idx"]),
+                                      _ptr(out["peak"]), _ptr(out.get("tau_hat")), _stream(stream, self.device)),
+              "fcc_tdoa_pcm_host")
         return out
 
     def geometry(self) -> dict:

@@ -165,6 +165,8 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_tc_bases);
     cudaFree(p->d_tc_peq);
     cudaFree(p->d_smooth_basis);
+    cudaFree(p->d_stft_tab);
+    pcm_destroy(p);
     for (int b = 0; b < 2; ++b) {
         cudaFree(p->d_stage[b]);
         cudaFree(p->d_stage_idx[b]);

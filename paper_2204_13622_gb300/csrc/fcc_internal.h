@@ -181,7 +181,9 @@ struct fcc_plan {
     // GCC baseline workspace, created lazily
     void *gcc_state = nullptr;
     // tensor-core (BF16 / FP16) path
-    float *d_smooth_basis = nullptr;   // smoothed path: [Q+1][2 kh], created on first use
+    float *d_smooth_basis = nullptr;   // smoothed path: [2 kh][QP], created on first use
+    float *d_stft_tab = nullptr;       // STFT front-end: twiddles and window, created on first use
+    void *pcm_state = nullptr;         // fcc_tdoa_pcm_host staging, created on first use
     void *d_tc_bases = nullptr;
     float *d_tc_peq = nullptr;
     int tc_F = 0;
@@ -215,6 +217,7 @@ inline fcc_status_t launch_tdoa(const fcc_plan *plan, const float2 *spectra, lon
     return plan->info.prec == FCC_PREC_FP32 ? launch_fp32(plan, spectra, T, idx, peak, tau, coef, corr, st)
                                             : launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
 }
+void pcm_destroy(fcc_plan *plan);
 fcc_status_t gcc_run(fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                      float *corr, cudaStream_t st);
 void gcc_destroy(fcc_plan *plan);

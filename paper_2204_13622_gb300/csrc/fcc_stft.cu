@@ -1,0 +1,399 @@
+// fcc_stft.cu -- the STFT front-end (Sec. 2 starts from the microphones' STFT
+// X_m(t, f)): periodic Hann window, frames of N samples every hop samples, and
+// per (frame, microphone) a real FFT of N points, done as an N/2-point complex
+// FFT of the packed samples z[j] = x[2j] + i x[2j + 1] followed by the split
+//   X[k] = E[k] + e^{-2 pi i k / N} O[k],  E = (Z[k] + Z*[H-k]) / 2,
+//   O = (Z[k] - Z*[H-k]) / 2i,  H = N/2, k = 0..H (Z periodic in H).
+// The complex FFT is the Stockham autosort form (radix-4 passes, then one
+// radix-2 pass when log2 H is odd): pass s reads x[j + r H/R], twiddles input r
+// by e^{-2 pi i k r / (Ns R)} with k = j mod Ns, takes the R-point DFT and
+// writes y[(j - k) R + k + r Ns]; Ns grows by R per pass and the output comes
+// out in natural order.
+//
+// stft_kernel<N>: one warp per (frame, microphone), two ping-pong buffers of H
+// complex values per warp in shared memory; twiddles and the window are tables
+// computed in FP64 on the host.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fcc_internal.h"
+#include "fcc_stft.h"
+
+namespace fcc {
+namespace {
+
+constexpr int kStftWarps = 8;
+constexpr long long kPcmChunkBytes = 64LL << 20;   // spectra per device chunk of fcc_tdoa_pcm
+constexpr long long kHostChunkFrames = 1LL << 16;  // frames per host chunk of fcc_tdoa_pcm_host
+
+struct StftParams {
+    const void *pcm;
+    int type;           // FCC_PCM_F32 or FCC_PCM_S16
+    long long T;
+    int M, hop;
+    const float *tab;   // [2H] FFT twiddles e^{-2 pi i m / H}, [2(H+1)] split twiddles e^{-2 pi i k / N}, [N] window
+    float2 *out;        // [T][M][H + 1]
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * kStftWarps) stft_kernel(const __grid_constant__ StftParams p)
+{
+    constexpr int H = N / 2, B = H + 1;
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2 *tw = reinterpret_cast<float2 *>(sm);  // [H]
+    float2 *sp = tw + H;                          // [H + 1], padded to H + 2
+    float *win = reinterpret_cast<float *>(sp + H + 2);
+    float2 *bufs = reinterpret_cast<float2 *>(win + N);  // [warps][2][H]
+    const float2 *tab2 = reinterpret_cast<const float2 *>(p.tab);
+    for (int e = threadIdx.x; e < H; e += blockDim.x) tw[e] = tab2[e];
+    for (int e = threadIdx.x; e <= H; e += blockDim.x) sp[e] = tab2[H + e];
+    for (int e = threadIdx.x; e < N; e += blockDim.x) win[e] = p.tab[2 * H + 2 * (H + 1) + e];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *b0 = bufs + (size_t)warp * 2 * H, *b1 = b0 + H;
+    const long long items = p.T * p.M;
+    const float *pf = static_cast<const float *>(p.pcm);
+    const short *ps = static_cast<const short *>(p.pcm);
+    for (long long it = (long long)blockIdx.x * kStftWarps + warp; it < items; it += (long long)gridDim.x * kStftWarps) {
+        const long long t = it / p.M;
+        const int m = (int)(it - t * p.M);
+        const long long s0 = t * p.hop;
+        // windowed samples: b0 viewed as N floats is z[j] = (x[2j], x[2j+1])
+        float *xr = reinterpret_cast<float *>(b0);
+#pragma unroll 4
+        for (int n = lane; n < N; n += 32) {
+            const size_t idx = (size_t)(s0 + n) * p.M + m;
+            const float v = p.type == FCC_PCM_F32 ? __ldg(pf + idx) : (float)__ldg(ps + idx) * (1.f / 32768.f);
+            xr[n] = win[n] * v;
+        }
+        __syncwarp();
+        float2 *src = b0, *dst = b1;
+        int Ns = 1;
+#pragma unroll
+        for (int pass = 0; pass < 16; ++pass) {
+            if (Ns * 4 > H) break;
+            for (int j = lane; j < H / 4; j += 32) {
+                const int k = j & (Ns - 1);
+                float2 v0 = src[j], v1 = src[j + H / 4], v2 = src[j + H / 2], v3 = src[j + 3 * (H / 4)];
+                if (Ns > 1) {
+                    const int u = k * (H / (4 * Ns));
+                    v1 = cmul(v1, tw[u]);
+                    v2 = cmul(v2, tw[2 * u]);
+                    v3 = cmul(v3, tw[3 * u]);
+                }
+                const float2 a = make_float2(v0.x + v2.x, v0.y + v2.y), b = make_float2(v0.x - v2.x, v0.y - v2.y);
+                const float2 c = make_float2(v1.x + v3.x, v1.y + v3.y), d = make_float2(v1.x - v3.x, v1.y - v3.y);
+                const int base = (j - k) * 4 + k;
+                dst[base] = make_float2(a.x + c.x, a.y + c.y);
+                dst[base + Ns] = make_float2(b.x + d.y, b.y - d.x);  // b - i d
+                dst[base + 2 * Ns] = make_float2(a.x - c.x, a.y - c.y);
+                dst[base + 3 * Ns] = make_float2(b.x - d.y, b.y + d.x);  // b + i d
+            }
+            __syncwarp();
+            float2 *tmp = src;
+            src = dst;
+            dst = tmp;
+            Ns *= 4;
+        }
+        if (Ns < H) {  // log2 H odd: one radix-2 pass
+            for (int j = lane; j < H / 2; j += 32) {
+                const int k = j & (Ns - 1);
+                const float2 v0 = src[j], v1 = cmul(src[j + H / 2], tw[k * (H / (2 * Ns))]);
+                const int base = (j - k) * 2 + k;
+                dst[base] = make_float2(v0.x + v1.x, v0.y + v1.y);
+                dst[base + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+            }
+            __syncwarp();
+            src = dst;
+        }
+        // split into the H + 1 bins of the real frame
+        float2 *out = p.out + (size_t)it * B;
+        for (int k = lane; k <= H; k += 32) {
+            const float2 zk = src[k & (H - 1)], zm = src[(H - k) & (H - 1)];
+            const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));  // (Z[k] - Z*[H-k]) / 2i
+            const float2 w = cmul(sp[k], O);
+            out[k] = make_float2(E.x + w.x, E.y + w.y);
+        }
+        __syncwarp();  // the buffers are reused by the next item
+    }
+}
+
+size_t stft_smem(int N)
+{
+    const int H = N / 2;
+    return (size_t)(H + H + 2) * sizeof(float2) + (size_t)N * sizeof(float) + (size_t)kStftWarps * 2 * H * sizeof(float2);
+}
+
+fcc_status_t stft_tables(fcc_plan *plan)
+{
+    if (plan->d_stft_tab) return FCC_OK;
+    const int N = plan->info.N, H = N / 2;
+    std::vector<float> tab((size_t)2 * H + 2 * (H + 1) + N);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int m = 0; m < H; ++m) {
+        tab[2 * m] = (float)std::cos(two_pi * m / H);
+        tab[2 * m + 1] = (float)-std::sin(two_pi * m / H);
+    }
+    for (int k = 0; k <= H; ++k) {
+        tab[2 * H + 2 * k] = (float)std::cos(two_pi * k / N);
+        tab[2 * H + 2 * k + 1] = (float)-std::sin(two_pi * k / N);
+    }
+    for (int n = 0; n < N; ++n) tab[2 * H + 2 * (H + 1) + n] = (float)(0.5 - 0.5 * std::cos(two_pi * n / N));
+    float *d = nullptr;
+    FCC_CUDA_TRY(dev_alloc((void **)&d, tab.size() * sizeof(float)));
+    cudaError_t e = cudaMemcpy(d, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(stft tables)");
+    }
+    plan->d_stft_tab = d;
+    return FCC_OK;
+}
+
+template <int N>
+fcc_status_t launch_stft_n(const StftParams &prm, int num_sms, cudaStream_t st)
+{
+    const size_t smem = stft_smem(N);
+    cudaError_t e = cudaFuncSetAttribute(stft_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(stft_kernel)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stft_kernel<N>, 32 * kStftWarps, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    const long long need = (prm.T * prm.M + kStftWarps - 1) / kStftWarps;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * std::max(per_sm, 1)));
+    stft_kernel<N><<<grid, 32 * kStftWarps, smem, st>>>(prm);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FCC_OK : cuda_fail(e, "stft_kernel launch");
+}
+
+fcc_status_t launch_stft(fcc_plan *plan, const void *pcm, int type, long long T, int hop, float2 *out, cudaStream_t st)
+{
+    fcc_status_t s = stft_tables(plan);
+    if (s != FCC_OK) return s;
+    StftParams prm{};
+    prm.pcm = pcm;
+    prm.type = type;
+    prm.T = T;
+    prm.M = plan->info.M;
+    prm.hop = hop;
+    prm.tab = plan->d_stft_tab;
+    prm.out = out;
+    switch (plan->info.N) {
+    case 64: return launch_stft_n<64>(prm, plan->num_sms, st);
+    case 128: return launch_stft_n<128>(prm, plan->num_sms, st);
+    case 256: return launch_stft_n<256>(prm, plan->num_sms, st);
+    case 512: return launch_stft_n<512>(prm, plan->num_sms, st);
+    case 1024: return launch_stft_n<1024>(prm, plan->num_sms, st);
+    case 2048: return launch_stft_n<2048>(prm, plan->num_sms, st);
+    default: return fail(FCC_ERR_UNSUPPORTED, "the STFT front-end needs 64 <= N <= 2048");
+    }
+}
+
+long long frames_of(long long n_samples, int N, int hop) { return n_samples < N ? 0 : 1 + (n_samples - N) / hop; }
+
+size_t sample_bytes(int type) { return type == FCC_PCM_S16 ? 2 : 4; }
+
+long long device_chunk(const fcc_plan *plan)
+{
+    const long long fb = (long long)plan->info.M * plan->info.B * 8;
+    return std::max<long long>(1, kPcmChunkBytes / fb);
+}
+
+fcc_status_t check_pcm(const fcc_plan *plan, int type, long long n_samples, int hop)
+{
+    if (type != FCC_PCM_F32 && type != FCC_PCM_S16) return fail(FCC_ERR_INVALID_ARG, "unknown PCM type");
+    if (n_samples < 0) return fail(FCC_ERR_INVALID_ARG, "n_samples < 0");
+    if (hop < 1) return fail(FCC_ERR_INVALID_ARG, "hop < 1");
+    if (plan->info.N < 64 || plan->info.N > 2048) return fail(FCC_ERR_UNSUPPORTED, "the STFT front-end needs 64 <= N <= 2048");
+    return FCC_OK;
+}
+
+// frames [t0, t0 + n) of the PCM: STFT into `spec`, then FCC into the outputs at t0
+fcc_status_t pcm_chunks(fcc_plan *plan, const unsigned char *pcm, int type, long long T, int hop, int *idx,
+                        float *peak, float *tau, float2 *spec, cudaStream_t st)
+{
+    const fcc_plan_info_t &in = plan->info;
+    const long long ch = device_chunk(plan);
+    const size_t sb = sample_bytes(type) * (size_t)in.M;
+    for (long long t0 = 0; t0 < T; t0 += ch) {
+        const long long n = std::min(ch, T - t0);
+        fcc_status_t s = launch_stft(plan, pcm + (size_t)t0 * hop * sb, type, n, hop, spec, st);
+        if (s != FCC_OK) return s;
+        const size_t o = (size_t)t0 * in.P;
+        s = launch_tdoa(plan, spec, n, idx + o, peak + o, tau ? tau + o : nullptr, nullptr, nullptr, st);
+        if (s != FCC_OK) return s;
+    }
+    return FCC_OK;
+}
+
+}  // namespace
+
+// Host-streaming state of fcc_tdoa_pcm_host, owned by the plan.
+struct PcmState {
+    void *d_pcm[2] = {nullptr, nullptr};
+    int *d_idx[2] = {nullptr, nullptr};
+    float *d_peak[2] = {nullptr, nullptr}, *d_tau[2] = {nullptr, nullptr};
+    float2 *d_spec = nullptr;
+    size_t pcm_cap = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev[5] = {};
+};
+
+void pcm_destroy(fcc_plan *plan)
+{
+    PcmState *s = static_cast<PcmState *>(plan->pcm_state);
+    if (!s) return;
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(s->d_pcm[b]);
+        cudaFree(s->d_idx[b]);
+        cudaFree(s->d_peak[b]);
+        cudaFree(s->d_tau[b]);
+    }
+    cudaFree(s->d_spec);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    for (auto &e : s->ev)
+        if (e) cudaEventDestroy(e);
+    delete s;
+    plan->pcm_state = nullptr;
+}
+
+}  // namespace fcc
+
+using namespace fcc;
+
+extern "C" {
+
+fcc_status_t fcc_stft_frames(const fcc_plan_t *plan, long long n_samples, int hop, long long *T)
+{
+    if (!plan || !T) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    if (n_samples < 0) return fail(FCC_ERR_INVALID_ARG, "n_samples < 0");
+    if (hop < 1) return fail(FCC_ERR_INVALID_ARG, "hop < 1");
+    *T = frames_of(n_samples, plan->info.N, hop);
+    return FCC_OK;
+}
+
+fcc_status_t fcc_stft(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, long long n_samples, int hop,
+                      void *d_spectra, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    fcc_status_t s = check_pcm(plan, type, n_samples, hop);
+    if (s != FCC_OK) return s;
+    const long long T = frames_of(n_samples, plan->info.N, hop);
+    if (T == 0) return FCC_OK;
+    if (!d_pcm || !d_spectra) return fail(FCC_ERR_INVALID_ARG, "null pcm/spectra");
+    if ((reinterpret_cast<uintptr_t>(d_pcm) & (sample_bytes(type) - 1)) || (reinterpret_cast<uintptr_t>(d_spectra) & 7))
+        return fail(FCC_ERR_INVALID_ARG, "misaligned buffer");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    return launch_stft(plan, d_pcm, type, T, hop, static_cast<float2 *>(d_spectra), static_cast<cudaStream_t>(stream));
+}
+
+fcc_status_t fcc_pcm_workspace(const fcc_plan_t *plan, long long n_samples, int hop, long long *bytes)
+{
+    if (!plan || !bytes) return fail(FCC_ERR_INVALID_ARG, "null argument");
+    if (n_samples < 0 || hop < 1) return fail(FCC_ERR_INVALID_ARG, "n_samples < 0 or hop < 1");
+    const long long T = frames_of(n_samples, plan->info.N, hop);
+    *bytes = std::min(T, device_chunk(plan)) * plan->info.M * plan->info.B * 8;
+    return FCC_OK;
+}
+
+fcc_status_t fcc_tdoa_pcm(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, long long n_samples, int hop,
+                          int *d_lag_idx, float *d_peak, float *d_tau_hat, void *d_work, long long work_bytes,
+                          void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    fcc_status_t s = check_pcm(plan, type, n_samples, hop);
+    if (s != FCC_OK) return s;
+    const long long T = frames_of(n_samples, plan->info.N, hop);
+    if (T == 0) return FCC_OK;
+    if (!d_pcm || !d_lag_idx || !d_peak || !d_work) return fail(FCC_ERR_INVALID_ARG, "null pcm/outputs/workspace");
+    if ((reinterpret_cast<uintptr_t>(d_pcm) & (sample_bytes(type) - 1)) || (reinterpret_cast<uintptr_t>(d_work) & 15) ||
+        ((reinterpret_cast<uintptr_t>(d_lag_idx) | reinterpret_cast<uintptr_t>(d_peak) |
+          reinterpret_cast<uintptr_t>(d_tau_hat)) & 3))
+        return fail(FCC_ERR_INVALID_ARG, "misaligned buffer");
+    long long need = 0;
+    fcc_pcm_workspace(plan, n_samples, hop, &need);
+    if (work_bytes < need) return fail(FCC_ERR_INVALID_ARG, "workspace too small");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    return pcm_chunks(plan, static_cast<const unsigned char *>(d_pcm), type, T, hop, d_lag_idx, d_peak, d_tau_hat,
+                      static_cast<float2 *>(d_work), static_cast<cudaStream_t>(stream));
+}
+
+fcc_status_t fcc_tdoa_pcm_host(fcc_plan_t *plan, const void *h_pcm, fcc_pcm_t type, long long n_samples, int hop,
+                               int *h_lag_idx, float *h_peak, float *h_tau_hat, void *stream)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    fcc_status_t s = check_pcm(plan, type, n_samples, hop);
+    if (s != FCC_OK) return s;
+    const fcc_plan_info_t &in = plan->info;
+    const long long T = frames_of(n_samples, in.N, hop);
+    if (T == 0) return FCC_OK;
+    if (!h_pcm || !h_lag_idx || !h_peak) return fail(FCC_ERR_INVALID_ARG, "null host buffer");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    DeviceScope scope(plan->device);
+    if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
+    const size_t sb = sample_bytes(type) * (size_t)in.M;
+    const long long hc = kHostChunkFrames;
+    const size_t pcm_bytes = ((size_t)(hc - 1) * hop + in.N) * sb;
+    PcmState *ps = static_cast<PcmState *>(plan->pcm_state);
+    if (!ps) {
+        ps = new (std::nothrow) PcmState;
+        if (!ps) return fail(FCC_ERR_OOM, "host allocation");
+        plan->pcm_state = ps;
+        for (int b = 0; b < 2; ++b) {
+            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_idx[b], (size_t)hc * in.P * sizeof(int)));
+            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_peak[b], (size_t)hc * in.P * sizeof(float)));
+            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_tau[b], (size_t)hc * in.P * sizeof(float)));
+        }
+        FCC_CUDA_TRY(dev_alloc((void **)&ps->d_spec, (size_t)std::min(hc, device_chunk(plan)) * in.M * in.B * 8));
+        FCC_CUDA_TRY(cudaStreamCreateWithFlags(&ps->copy, cudaStreamNonBlocking));
+        for (auto &e : ps->ev) FCC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (ps->pcm_cap < pcm_bytes) {
+        FCC_CUDA_TRY(cudaDeviceSynchronize());
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(ps->d_pcm[b]);
+            ps->d_pcm[b] = nullptr;
+        }
+        ps->pcm_cap = 0;
+        for (int b = 0; b < 2; ++b) FCC_CUDA_TRY(dev_alloc(&ps->d_pcm[b], pcm_bytes));
+        ps->pcm_cap = pcm_bytes;
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaStream_t hs = ps->copy;
+    // ev[b]: PCM of buffer b on the device; ev[2 + b]: buffer b free again
+    FCC_CUDA_TRY(cudaEventRecord(ps->ev[4], cs));
+    FCC_CUDA_TRY(cudaStreamWaitEvent(hs, ps->ev[4], 0));
+    const unsigned char *src = static_cast<const unsigned char *>(h_pcm);
+    long long chunk_id = 0;
+    for (long long t0 = 0; t0 < T; t0 += hc, ++chunk_id) {
+        const int b = (int)(chunk_id & 1);
+        const long long n = std::min(hc, T - t0);
+        const size_t bytes = ((size_t)(n - 1) * hop + in.N) * sb;
+        if (chunk_id >= 2) FCC_CUDA_TRY(cudaStreamWaitEvent(hs, ps->ev[2 + b], 0));
+        FCC_CUDA_TRY(cudaMemcpyAsync(ps->d_pcm[b], src + (size_t)t0 * hop * sb, bytes, cudaMemcpyHostToDevice, hs));
+        FCC_CUDA_TRY(cudaEventRecord(ps->ev[b], hs));
+        FCC_CUDA_TRY(cudaStreamWaitEvent(cs, ps->ev[b], 0));
+        s = pcm_chunks(plan, static_cast<const unsigned char *>(ps->d_pcm[b]), type, n, hop, ps->d_idx[b],
+                       ps->d_peak[b], h_tau_hat ? ps->d_tau[b] : nullptr, ps->d_spec, cs);
+        if (s != FCC_OK) return s;
+        const size_t o = (size_t)t0 * in.P, cnt = (size_t)n * in.P;
+        FCC_CUDA_TRY(cudaMemcpyAsync(h_lag_idx + o, ps->d_idx[b], cnt * sizeof(int), cudaMemcpyDeviceToHost, cs));
+        FCC_CUDA_TRY(cudaMemcpyAsync(h_peak + o, ps->d_peak[b], cnt * sizeof(float), cudaMemcpyDeviceToHost, cs));
+        if (h_tau_hat)
+            FCC_CUDA_TRY(cudaMemcpyAsync(h_tau_hat + o, ps->d_tau[b], cnt * sizeof(float), cudaMemcpyDeviceToHost, cs));
+        FCC_CUDA_TRY(cudaEventRecord(ps->ev[2 + b], cs));
+    }
+    return fcc_plan_sync(plan, stream);
+}
+
+}  // extern "C"

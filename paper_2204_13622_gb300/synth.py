@@ -79,6 +79,38 @@ def fibonacci_directions(n: int, hemisphere: bool = True) -> np.ndarray:
     return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
 
 
+def pcm_far_field(n_samples: int, xyz: np.ndarray, fs: float, seed: int, device="cpu", segment: int = 16000,
+                  snr_db: float = 10.0, kind: str = "s16", c: float = SPEED_OF_SOUND):
+    """Interleaved multichannel PCM [n_samples, M] (int16 or float32): per
+    segment of `segment` samples one far-field white source from a seeded
+    random direction (azimuth U[0, 2 pi), elevation U[0, pi/2]), seen by each
+    mic with its delay rounded to whole samples, plus white noise at `snr_db`.
+    Generated with torch on `device`."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(int(seed))
+    M = xyz.shape[0]
+    n_seg = (n_samples + segment - 1) // segment
+    az = torch.rand(n_seg, generator=g, dtype=torch.float64) * 2 * math.pi
+    el = torch.rand(n_seg, generator=g, dtype=torch.float64) * math.pi / 2
+    u = torch.stack([torch.cos(el) * torch.cos(az), torch.cos(el) * torch.sin(az), torch.sin(el)], 1)
+    d = torch.round(-fs * (u @ torch.from_numpy(np.asarray(xyz, np.float64)).T) / c).to(torch.int64)  # [n_seg, M]
+    pad = int(d.abs().max()) + 1
+    gd = torch.Generator(device=device).manual_seed(int(seed) + 1)
+    src = torch.randn(n_samples + 2 * pad, generator=gd, device=device)
+    seg = torch.arange(n_samples, device=device) // segment
+    out = torch.empty((n_samples, M), dtype=torch.int16 if kind == "s16" else torch.float32, device=device)
+    amp_n = 10.0 ** (-snr_db / 20.0)
+    dd = d.to(device)
+    for m in range(M):
+        x = src[torch.arange(n_samples, device=device) + pad - dd[seg, m]]
+        x = x + amp_n * torch.randn(n_samples, generator=gd, device=device)
+        if kind == "s16":
+            out[:, m] = torch.clamp(torch.round(x * 6000.0), -32768, 32767).to(torch.int16)
+        else:
+            out[:, m] = x
+    return out
+
+
 def far_field_delays(xyz: np.ndarray, direction: np.ndarray, fs: float,
                      c: float = SPEED_OF_SOUND) -> np.ndarray:
     """Per-mic delay (samples) of a far-field source from `direction`."""

@@ -63,6 +63,13 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.fcc_doa_workspace(None, 10, None) == 1
     assert lib.fcc_tdoa_doa(None, None, 0, None, None, None, None, None, 0, None) == 1
     lib.fcc_doa_destroy(None)  # no-op
+    # STFT front-end entry points
+    T = ctypes.c_longlong()
+    assert lib.fcc_stft_frames(None, 10, 4, ctypes.byref(T)) == 1
+    assert lib.fcc_stft(None, None, 0, 0, 1, None, None) == 1
+    assert lib.fcc_pcm_workspace(None, 10, 4, None) == 1
+    assert lib.fcc_tdoa_pcm(None, None, 0, 0, 1, None, None, None, None, 0, None) == 1
+    assert lib.fcc_tdoa_pcm_host(None, None, 0, 0, 1, None, None, None, None) == 1
 
 
 def test_debug_hooks_validate_arguments(lib):
