@@ -38,15 +38,18 @@ fcc_status_t fcc_stft_frames(const fcc_plan_t *plan, long long n_samples, int ho
 fcc_status_t fcc_stft(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, long long n_samples, int hop,
                       void *d_spectra, void *stream);
 
-/* Bytes of device workspace fcc_tdoa_pcm needs (a chunk of spectra). */
+/* Bytes of device workspace recommended for fcc_tdoa_pcm: one chunk of spectra.
+ * fcc_tdoa_pcm accepts any workspace of at least one frame of spectra (M (N/2+1)
+ * 8 bytes) and processes the frames in chunks of as many as it holds. */
 fcc_status_t fcc_pcm_workspace(const fcc_plan_t *plan, long long n_samples, int hop, long long *bytes);
 
 /*
- * PCM in, TDoA out: fcc_stft then fcc_tdoa chunk by chunk through d_work (at
- * least fcc_pcm_workspace bytes, 16-byte aligned), so the spectra never make a
- * round trip through HBM.  Outputs as fcc_tdoa ([T][P]; d_tau_hat may be NULL).
- * Asynchronous on `stream`; device conditions (NaN / Inf samples) go to the
- * plan's error word (fcc_plan_sync).
+ * PCM in, TDoA out: fcc_stft then fcc_tdoa chunk by chunk through d_work
+ * (16-byte aligned, at least one frame of spectra; the recommended size is
+ * fcc_pcm_workspace), the spectra of a chunk going from one kernel to the next.
+ * Outputs as fcc_tdoa ([T][P]; d_tau_hat may be NULL).  Asynchronous on
+ * `stream`; device conditions (NaN / Inf samples) go to the plan's error word
+ * (fcc_plan_sync).
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
  */
 fcc_status_t fcc_tdoa_pcm(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, long long n_samples, int hop,

@@ -4,15 +4,18 @@
 // FFT of the packed samples z[j] = x[2j] + i x[2j + 1] followed by the split
 //   X[k] = E[k] + e^{-2 pi i k / N} O[k],  E = (Z[k] + Z*[H-k]) / 2,
 //   O = (Z[k] - Z*[H-k]) / 2i,  H = N/2, k = 0..H (Z periodic in H).
-// The complex FFT is the Stockham autosort form (radix-4 passes, then one
-// radix-2 pass when log2 H is odd): pass s reads x[j + r H/R], twiddles input r
-// by e^{-2 pi i k r / (Ns R)} with k = j mod Ns, takes the R-point DFT and
-// writes y[(j - k) R + k + r Ns]; Ns grows by R per pass and the output comes
-// out in natural order.
+// The complex FFT of H = 32 R1 points is the four-step form with n = 32 n1 + n2
+// and k = k1 + R1 k2: lane n2 holds z[32 n1 + n2] for n1 < R1 in registers,
+//   1. an R1-point DFT over n1 in registers (radix-2, decimation in frequency:
+//      register r ends with k1 = bitrev(r));
+//   2. the twiddle W_H^{n2 k1};
+//   3. a 32-point DFT over n2 across the warp's lanes (five radix-2 stages with
+//      butterfly partners from __shfl_xor_sync; lane p ends with k2 = bitrev(p));
+//   4. one store into shared memory at index i + i / R1 (bank-conflict free for a
+//      fixed register), then the split above reads Z[k] and Z[H - k].
 //
-// stft_kernel<N>: one warp per (frame, microphone), two ping-pong buffers of H
-// complex values per warp in shared memory; twiddles and the window are tables
-// computed in FP64 on the host.
+// stft_kernel<N, S>: one warp per (frame, microphone); twiddles and the window
+// are tables computed in FP64 on the host.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -24,7 +27,10 @@ namespace fcc {
 namespace {
 
 constexpr int kStftWarps = 8;
-constexpr long long kPcmChunkBytes = 64LL << 20;   // spectra per device chunk of fcc_tdoa_pcm
+// spectra per device chunk (recommended workspace): measured on the 8-mic circle,
+// 2^20 frames, per step: 64 MB 22.4 ms, 256 MB 19.2 ms, 1 GB 18.0 ms, 4 GB 17.6 ms
+// (fewer launches count for more than keeping a chunk in L2)
+constexpr long long kPcmChunkBytes = 1LL << 30;
 constexpr long long kHostChunkFrames = 1LL << 16;  // frames per host chunk of fcc_tdoa_pcm_host
 
 struct StftParams {
@@ -41,94 +47,103 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-template <int N>
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+__host__ __device__ constexpr int bitrev(int x, int bits) { return bits == 0 ? 0 : ((x & 1) << (bits - 1)) | bitrev(x >> 1, bits - 1); }
+
+template <int N, typename S>
 __global__ void __launch_bounds__(32 * kStftWarps) stft_kernel(const __grid_constant__ StftParams p)
 {
-    constexpr int H = N / 2, B = H + 1;
+    constexpr int H = N / 2, B = H + 1, R1 = H / 32, LB = ilog2(R1);
     extern __shared__ __align__(16) unsigned char sm[];
-    float2 *tw = reinterpret_cast<float2 *>(sm);  // [H]
-    float2 *sp = tw + H;                          // [H + 1], padded to H + 2
+    float2 *tw = reinterpret_cast<float2 *>(sm);  // [H]: W_H^m
+    float2 *sp = tw + H;                          // [H + 1]: W_N^k, padded to H + 2
     float *win = reinterpret_cast<float *>(sp + H + 2);
-    float2 *bufs = reinterpret_cast<float2 *>(win + N);  // [warps][2][H]
+    float2 *bufs = reinterpret_cast<float2 *>(win + N);  // [warps][H + 32]
     const float2 *tab2 = reinterpret_cast<const float2 *>(p.tab);
     for (int e = threadIdx.x; e < H; e += blockDim.x) tw[e] = tab2[e];
     for (int e = threadIdx.x; e <= H; e += blockDim.x) sp[e] = tab2[H + e];
     for (int e = threadIdx.x; e < N; e += blockDim.x) win[e] = p.tab[2 * H + 2 * (H + 1) + e];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *b0 = bufs + (size_t)warp * 2 * H, *b1 = b0 + H;
+    const unsigned FULLM = 0xffffffffu;
+    float2 *buf = bufs + (size_t)warp * (H + 32);
+    const float2 *win2 = reinterpret_cast<const float2 *>(win);
+    // per-lane twiddles of the cross-lane stages h = 16, 8, 4, 2 (lower lanes W_{2h}^{p mod h}, upper 1)
+    float2 ct[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int h = 16 >> s;
+        ct[s] = (lane & h) ? tw[(lane % h) * (16 / h) * (H / 32)] : make_float2(1.f, 0.f);
+    }
+    const int k2 = (int)(__brev((unsigned)lane) >> 27);
+    const float scale = sizeof(S) == 2 ? 1.f / 32768.f : 1.f;
     const long long items = p.T * p.M;
-    const float *pf = static_cast<const float *>(p.pcm);
-    const short *ps = static_cast<const short *>(p.pcm);
+    const S *pcm = static_cast<const S *>(p.pcm);
     for (long long it = (long long)blockIdx.x * kStftWarps + warp; it < items; it += (long long)gridDim.x * kStftWarps) {
         const long long t = it / p.M;
         const int m = (int)(it - t * p.M);
-        const long long s0 = t * p.hop;
-        // windowed samples: b0 viewed as N floats is z[j] = (x[2j], x[2j+1])
-        float *xr = reinterpret_cast<float *>(b0);
-#pragma unroll 4
-        for (int n = lane; n < N; n += 32) {
-            const size_t idx = (size_t)(s0 + n) * p.M + m;
-            const float v = p.type == FCC_PCM_F32 ? __ldg(pf + idx) : (float)__ldg(ps + idx) * (1.f / 32768.f);
-            xr[n] = win[n] * v;
+        const S *x = pcm + (size_t)(t * p.hop) * p.M + m;
+        float2 v[R1];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const int j = 32 * r + lane;  // z[j] = (w x)[2j] + i (w x)[2j + 1]
+            const float2 w = win2[j];
+            v[r] = make_float2(w.x * scale * (float)x[(size_t)(2 * j) * p.M], w.y * scale * (float)x[(size_t)(2 * j + 1) * p.M]);
+        }
+        // 1. R1-point DFT over n1 (decimation in frequency)
+#pragma unroll
+        for (int h = R1 / 2; h >= 1; h /= 2) {
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                if (r & h) continue;
+                const float2 a = v[r], b = v[r + h];
+                const int i = r % h;
+                v[r] = make_float2(a.x + b.x, a.y + b.y);
+                const float2 d = make_float2(a.x - b.x, a.y - b.y);
+                v[r + h] = i == 0 ? d : cmul(d, tw[i * (H / (2 * h))]);
+            }
+        }
+        // 2. twiddle W_H^{n2 k1}
+#pragma unroll
+        for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], tw[lane * bitrev(r, LB)]);
+        // 3. 32-point DFT across the lanes
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int h = 16 >> s;
+            const float sg = (lane & h) ? -1.f : 1.f;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) {
+                const float ox = __shfl_xor_sync(FULLM, v[r].x, h), oy = __shfl_xor_sync(FULLM, v[r].y, h);
+                float2 tv = make_float2(fmaf(sg, v[r].x, ox), fmaf(sg, v[r].y, oy));
+                if (s < 4) tv = cmul(tv, ct[s]);
+                v[r] = tv;
+            }
+        }
+        // 4. Z[k1 + R1 k2] into the buffer at index i + i / R1
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const int i = bitrev(r, LB) + R1 * k2;
+            buf[i + (i >> LB)] = v[r];
         }
         __syncwarp();
-        float2 *src = b0, *dst = b1;
-        int Ns = 1;
-#pragma unroll
-        for (int pass = 0; pass < 16; ++pass) {
-            if (Ns * 4 > H) break;
-            for (int j = lane; j < H / 4; j += 32) {
-                const int k = j & (Ns - 1);
-                float2 v0 = src[j], v1 = src[j + H / 4], v2 = src[j + H / 2], v3 = src[j + 3 * (H / 4)];
-                if (Ns > 1) {
-                    const int u = k * (H / (4 * Ns));
-                    v1 = cmul(v1, tw[u]);
-                    v2 = cmul(v2, tw[2 * u]);
-                    v3 = cmul(v3, tw[3 * u]);
-                }
-                const float2 a = make_float2(v0.x + v2.x, v0.y + v2.y), b = make_float2(v0.x - v2.x, v0.y - v2.y);
-                const float2 c = make_float2(v1.x + v3.x, v1.y + v3.y), d = make_float2(v1.x - v3.x, v1.y - v3.y);
-                const int base = (j - k) * 4 + k;
-                dst[base] = make_float2(a.x + c.x, a.y + c.y);
-                dst[base + Ns] = make_float2(b.x + d.y, b.y - d.x);  // b - i d
-                dst[base + 2 * Ns] = make_float2(a.x - c.x, a.y - c.y);
-                dst[base + 3 * Ns] = make_float2(b.x - d.y, b.y + d.x);  // b + i d
-            }
-            __syncwarp();
-            float2 *tmp = src;
-            src = dst;
-            dst = tmp;
-            Ns *= 4;
-        }
-        if (Ns < H) {  // log2 H odd: one radix-2 pass
-            for (int j = lane; j < H / 2; j += 32) {
-                const int k = j & (Ns - 1);
-                const float2 v0 = src[j], v1 = cmul(src[j + H / 2], tw[k * (H / (2 * Ns))]);
-                const int base = (j - k) * 2 + k;
-                dst[base] = make_float2(v0.x + v1.x, v0.y + v1.y);
-                dst[base + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
-            }
-            __syncwarp();
-            src = dst;
-        }
         // split into the H + 1 bins of the real frame
         float2 *out = p.out + (size_t)it * B;
         for (int k = lane; k <= H; k += 32) {
-            const float2 zk = src[k & (H - 1)], zm = src[(H - k) & (H - 1)];
+            const int i0 = k & (H - 1), i1 = (H - k) & (H - 1);
+            const float2 zk = buf[i0 + (i0 >> LB)], zm = buf[i1 + (i1 >> LB)];
             const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));  // (Z[k] - Z*[H-k]) / 2i
             const float2 w = cmul(sp[k], O);
             out[k] = make_float2(E.x + w.x, E.y + w.y);
         }
-        __syncwarp();  // the buffers are reused by the next item
+        __syncwarp();  // the buffer is reused by the next item
     }
 }
 
 size_t stft_smem(int N)
 {
     const int H = N / 2;
-    return (size_t)(H + H + 2) * sizeof(float2) + (size_t)N * sizeof(float) + (size_t)kStftWarps * 2 * H * sizeof(float2);
+    return (size_t)(H + H + 2) * sizeof(float2) + (size_t)N * sizeof(float) + (size_t)kStftWarps * (H + 32) * sizeof(float2);
 }
 
 fcc_status_t stft_tables(fcc_plan *plan)
@@ -157,20 +172,26 @@ fcc_status_t stft_tables(fcc_plan *plan)
     return FCC_OK;
 }
 
-template <int N>
+template <int N, typename S>
 fcc_status_t launch_stft_n(const StftParams &prm, int num_sms, cudaStream_t st)
 {
     const size_t smem = stft_smem(N);
-    cudaError_t e = cudaFuncSetAttribute(stft_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(stft_kernel<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(stft_kernel)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stft_kernel<N>, 32 * kStftWarps, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stft_kernel<N, S>, 32 * kStftWarps, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     const long long need = (prm.T * prm.M + kStftWarps - 1) / kStftWarps;
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)num_sms * std::max(per_sm, 1)));
-    stft_kernel<N><<<grid, 32 * kStftWarps, smem, st>>>(prm);
+    stft_kernel<N, S><<<grid, 32 * kStftWarps, smem, st>>>(prm);
     e = cudaGetLastError();
     return e == cudaSuccess ? FCC_OK : cuda_fail(e, "stft_kernel launch");
+}
+
+template <int N>
+fcc_status_t launch_stft_t(const StftParams &prm, int num_sms, cudaStream_t st)
+{
+    return prm.type == FCC_PCM_S16 ? launch_stft_n<N, short>(prm, num_sms, st) : launch_stft_n<N, float>(prm, num_sms, st);
 }
 
 fcc_status_t launch_stft(fcc_plan *plan, const void *pcm, int type, long long T, int hop, float2 *out, cudaStream_t st)
@@ -186,12 +207,12 @@ fcc_status_t launch_stft(fcc_plan *plan, const void *pcm, int type, long long T,
     prm.tab = plan->d_stft_tab;
     prm.out = out;
     switch (plan->info.N) {
-    case 64: return launch_stft_n<64>(prm, plan->num_sms, st);
-    case 128: return launch_stft_n<128>(prm, plan->num_sms, st);
-    case 256: return launch_stft_n<256>(prm, plan->num_sms, st);
-    case 512: return launch_stft_n<512>(prm, plan->num_sms, st);
-    case 1024: return launch_stft_n<1024>(prm, plan->num_sms, st);
-    case 2048: return launch_stft_n<2048>(prm, plan->num_sms, st);
+    case 64: return launch_stft_t<64>(prm, plan->num_sms, st);
+    case 128: return launch_stft_t<128>(prm, plan->num_sms, st);
+    case 256: return launch_stft_t<256>(prm, plan->num_sms, st);
+    case 512: return launch_stft_t<512>(prm, plan->num_sms, st);
+    case 1024: return launch_stft_t<1024>(prm, plan->num_sms, st);
+    case 2048: return launch_stft_t<2048>(prm, plan->num_sms, st);
     default: return fail(FCC_ERR_UNSUPPORTED, "the STFT front-end needs 64 <= N <= 2048");
     }
 }
@@ -215,12 +236,11 @@ fcc_status_t check_pcm(const fcc_plan *plan, int type, long long n_samples, int 
     return FCC_OK;
 }
 
-// frames [t0, t0 + n) of the PCM: STFT into `spec`, then FCC into the outputs at t0
+// frames [t0, t0 + n) of the PCM, ch at a time: STFT into `spec`, then FCC into the outputs at t0
 fcc_status_t pcm_chunks(fcc_plan *plan, const unsigned char *pcm, int type, long long T, int hop, int *idx,
-                        float *peak, float *tau, float2 *spec, cudaStream_t st)
+                        float *peak, float *tau, float2 *spec, long long ch, cudaStream_t st)
 {
     const fcc_plan_info_t &in = plan->info;
-    const long long ch = device_chunk(plan);
     const size_t sb = sample_bytes(type) * (size_t)in.M;
     for (long long t0 = 0; t0 < T; t0 += ch) {
         const long long n = std::min(ch, T - t0);
@@ -318,14 +338,15 @@ fcc_status_t fcc_tdoa_pcm(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, l
         ((reinterpret_cast<uintptr_t>(d_lag_idx) | reinterpret_cast<uintptr_t>(d_peak) |
           reinterpret_cast<uintptr_t>(d_tau_hat)) & 3))
         return fail(FCC_ERR_INVALID_ARG, "misaligned buffer");
-    long long need = 0;
-    fcc_pcm_workspace(plan, n_samples, hop, &need);
-    if (work_bytes < need) return fail(FCC_ERR_INVALID_ARG, "workspace too small");
+    // the workspace holds one chunk of spectra: a larger one means fewer, larger chunks
+    const long long frame_bytes = (long long)plan->info.M * plan->info.B * 8;
+    if (work_bytes < frame_bytes) return fail(FCC_ERR_INVALID_ARG, "workspace smaller than one frame of spectra");
     if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
     DeviceScope scope(plan->device);
     if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
     return pcm_chunks(plan, static_cast<const unsigned char *>(d_pcm), type, T, hop, d_lag_idx, d_peak, d_tau_hat,
-                      static_cast<float2 *>(d_work), static_cast<cudaStream_t>(stream));
+                      static_cast<float2 *>(d_work), std::min(T, work_bytes / frame_bytes),
+                      static_cast<cudaStream_t>(stream));
 }
 
 fcc_status_t fcc_tdoa_pcm_host(fcc_plan_t *plan, const void *h_pcm, fcc_pcm_t type, long long n_samples, int hop,
@@ -384,7 +405,8 @@ fcc_status_t fcc_tdoa_pcm_host(fcc_plan_t *plan, const void *h_pcm, fcc_pcm_t ty
         FCC_CUDA_TRY(cudaEventRecord(ps->ev[b], hs));
         FCC_CUDA_TRY(cudaStreamWaitEvent(cs, ps->ev[b], 0));
         s = pcm_chunks(plan, static_cast<const unsigned char *>(ps->d_pcm[b]), type, n, hop, ps->d_idx[b],
-                       ps->d_peak[b], h_tau_hat ? ps->d_tau[b] : nullptr, ps->d_spec, cs);
+                       ps->d_peak[b], h_tau_hat ? ps->d_tau[b] : nullptr, ps->d_spec,
+                       std::min(hc, device_chunk(plan)), cs);
         if (s != FCC_OK) return s;
         const size_t o = (size_t)t0 * in.P, cnt = (size_t)n * in.P;
         FCC_CUDA_TRY(cudaMemcpyAsync(h_lag_idx + o, ps->d_idx[b], cnt * sizeof(int), cudaMemcpyDeviceToHost, cs));
