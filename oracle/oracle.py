@@ -218,6 +218,34 @@ class Basis:
         self.WK = lowrank(self.U, self.s, self.V, self.K)
 
 
+class BasisB:
+    """The second basis split of the problem statement (real part of the
+    cross-spectrum on cosine bases, imaginary part on sine bases; the paper
+    itself folds, Eqs. 6-9): with C = Re W and S = Im W (Eq. 3),
+        y_B = 2 (C_Kc Re x - S_Ks Im x) = 2 Re{(C_Kc + j S_Ks) x},
+    where C_Kc and S_Ks are each truncated from the oracle's own Jacobi SVD of
+    that matrix, K by the energy rule applied to its own singular values (Sec. 4
+    rule), or given.  `WK` is the complex operator C_Kc + j S_Ks, so `tdoa` and
+    `tdoa_smoothed` compute form B unchanged."""
+
+    def __init__(self, N: int, L: int, den: int, Kc: int | None = None, Ks: int | None = None,
+                 energy: float = 0.999):
+        self.N, self.L, self.den = N, L, den
+        self.B = N // 2 + 1
+        self.taus = grid(L, den)
+        self.I = len(self.taus)
+        self.delta = 1.0 / den
+        W = build_W(N, self.taus)
+        self.C, self.S = np.ascontiguousarray(W.real), np.ascontiguousarray(W.imag)
+        self.Uc, self.sc, self.Vc = svd(self.C)
+        self.Us, self.ss, self.Vs = svd(self.S)
+        self.Kc = rank_energy(self.sc, energy) if Kc is None else int(Kc)
+        self.Ks = rank_energy(self.ss, energy) if Ks is None else int(Ks)
+        self.CK = lowrank(self.Uc, self.sc, self.Vc, self.Kc).real
+        self.SK = lowrank(self.Us, self.ss, self.Vs, self.Ks).real
+        self.WK = self.CK + 1j * self.SK
+
+
 def tdoa(X: np.ndarray, W: np.ndarray, taus: np.ndarray, delta: float, want_y: bool = False,
          threads: int | None = None):
     """The per-pair-frame pipeline over spectra X[T, M, N/2+1] (complex64).
