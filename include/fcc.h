@@ -55,6 +55,12 @@ typedef enum {
     FCC_PREC_FP16 = 2   /* projection operands in FP16, FP32 accumulation (tensor cores) */
 } fcc_prec_t;
 
+typedef enum {
+    FCC_FORM_FOLDED = 0,     /* the paper's even/odd bases on the folded x_s, x_d (Eqs. 6-9) */
+    FCC_FORM_REIM_SPLIT = 1  /* cosine bases on Re x and sine bases on Im x: C = Re W and
+                                S = Im W (Eq. 3) truncated by their own SVDs; y = 2 (C_K Re x - S_K Im x) */
+} fcc_form_t;
+
 /*
  * Plan description (Sec. 3 grid, Sec. 4 rank).  All fields are copied.
  *   n_mics   M, 2 <= M <= 16.
@@ -71,6 +77,13 @@ typedef enum {
  *            are kept too.
  *   prec     an fcc_prec_t.
  *   device   CUDA device ordinal; < 0 uses the calling thread's current device.
+ *   form     an fcc_form_t (0, the default, is the paper's folded form).  The
+ *            split form is FP32 only and runs on the per-pair kernel of
+ *            fcc_smooth.h (an even number of mics up to 8, 128 <= N <= 512); its
+ *            info reports K_even = K_c (cosine bases) and K_odd = K_s (sine
+ *            bases), each chosen by the energy rule on its own matrix (or both
+ *            = K when K > 0), and fcc_tdoa gives no coefficient or correlation
+ *            output for it.
  */
 typedef struct {
     int n_mics;
@@ -84,6 +97,7 @@ typedef struct {
     double energy;
     int prec;
     int device;
+    int form;
 } fcc_plan_desc_t;
 
 /* Sizes of a plan; K = K_even + K_odd (even/odd bases of Eq. 6). */
@@ -94,6 +108,7 @@ typedef struct {
     int prec;
     double delta;           /* grid step 1/den */
     double fs, c;
+    int form;               /* fcc_form_t */
 } fcc_plan_info_t;
 
 typedef struct fcc_plan fcc_plan_t;
@@ -136,6 +151,9 @@ fcc_status_t fcc_plan_singular_values(const fcc_plan_t *plan, double *s_even, in
  *                    common phase exp(j pi tau / 2) factored out.
  * With z_e = Pe x_s and z_o = Po x_d (complex), the correlation is
  *   y(tau_i) = 2 Re{ exp(j pi tau_i / 2) (Ue z_e + j Uo z_o)[i] }.
+ * For FCC_FORM_REIM_SPLIT plans: Pe[K_c][N/2+1] and Po[K_s][N/2+1] are the
+ * cosine and sine projections (sigma_k v_k of C and S), Ue[I][K_c] and Uo[I][K_s]
+ * their left vectors, and y = 2 (Ue (Pe Re x) - Uo (Po Im x)).
  */
 fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, double *Ue, double *Uo);
 

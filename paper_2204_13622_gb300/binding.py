@@ -19,6 +19,7 @@ FCC_OK = 0
 STATUS = {0: "FCC_OK", 1: "FCC_ERR_INVALID_ARG", 2: "FCC_ERR_UNSUPPORTED", 3: "FCC_ERR_OOM",
           4: "FCC_ERR_CUDA", 5: "FCC_ERR_TIMEOUT", 6: "FCC_ERR_NONFINITE", 7: "FCC_ERR_NOT_CONVERGED"}
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
+FORM = {"folded": 0, "reim": 1}
 
 # every symbol include/fcc.h declares
 EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_taus",
@@ -47,7 +48,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("n_mics", ctypes.c_int), ("mic_xyz", ctypes.POINTER(ctypes.c_double)),
                 ("fs", ctypes.c_double), ("N", ctypes.c_int), ("c", ctypes.c_double),
                 ("tau_max", ctypes.c_double), ("lag_den", ctypes.c_int), ("K", ctypes.c_int),
-                ("energy", ctypes.c_double), ("prec", ctypes.c_int), ("device", ctypes.c_int)]
+                ("energy", ctypes.c_double), ("prec", ctypes.c_int), ("device", ctypes.c_int),
+                ("form", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -55,7 +57,7 @@ class PlanInfo(ctypes.Structure):
                 ("Q", ctypes.c_int), ("L", ctypes.c_int), ("den", ctypes.c_int), ("I", ctypes.c_int),
                 ("center", ctypes.c_int), ("K", ctypes.c_int), ("K_even", ctypes.c_int),
                 ("K_odd", ctypes.c_int), ("prec", ctypes.c_int), ("delta", ctypes.c_double),
-                ("fs", ctypes.c_double), ("c", ctypes.c_double)]
+                ("fs", ctypes.c_double), ("c", ctypes.c_double), ("form", ctypes.c_int)]
 
 
 class Geometry(ctypes.Structure):
@@ -201,7 +203,7 @@ class Plan:
 
     def __init__(self, n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0,
                  mic_xyz=None, c: float = 343.0, K: int = 0, energy: float = 0.999,
-                 prec: str = "fp32", device: int | None = None):
+                 prec: str = "fp32", device: int | None = None, form: str = "folded"):
         import torch
         if device is None:
             device = torch.cuda.current_device()
@@ -211,7 +213,7 @@ class Plan:
             xyz = np.ascontiguousarray(mic_xyz, np.float64).reshape(n_mics, 3)
         desc = PlanDesc(n_mics, xyz.ctypes.data_as(_dp) if xyz is not None else None, float(fs), int(N),
                         float(c), float(tau_max), int(lag_den), int(K), float(energy), PREC[prec],
-                        self.device)
+                        self.device, FORM[form])
         h = _vp()
         check(lib().fcc_plan_create(ctypes.byref(desc), ctypes.byref(h)), "fcc_plan_create")
         self._h = h
@@ -253,7 +255,10 @@ class Plan:
 
     def bases(self):
         KE, KO, Q, I = self.K_even, self.K_odd, self.Q, self.I
-        Pe, Po = np.empty((KE, Q + 1)), np.empty((KO, Q))
+        if self.form == FORM["reim"]:  # cosine / sine bases over all N/2 + 1 bins
+            Pe, Po = np.empty((KE, self.B)), np.empty((KO, self.B))
+        else:
+            Pe, Po = np.empty((KE, Q + 1)), np.empty((KO, Q))
         Ue, Uo = np.empty((I, KE)), np.empty((I, KO))
         check(lib().fcc_plan_bases(self._h, Pe.ctypes.data_as(_dp), Po.ctypes.data_as(_dp),
                                    Ue.ctypes.data_as(_dp), Uo.ctypes.data_as(_dp)), "fcc_plan_bases")

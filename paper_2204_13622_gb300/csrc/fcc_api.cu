@@ -194,6 +194,9 @@ fcc_status_t fcc::plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t 
         return fail(FCC_ERR_INVALID_ARG, "N must be a power of two in [16, 4096]");
     if (d->lag_den < 1 || d->lag_den > 64) return fail(FCC_ERR_INVALID_ARG, "lag_den out of [1, 64]");
     if (d->prec < FCC_PREC_FP32 || d->prec > FCC_PREC_FP16) return fail(FCC_ERR_INVALID_ARG, "prec");
+    if (d->form != FCC_FORM_FOLDED && d->form != FCC_FORM_REIM_SPLIT) return fail(FCC_ERR_INVALID_ARG, "form");
+    if (d->form == FCC_FORM_REIM_SPLIT && d->prec != FCC_PREC_FP32)
+        return fail(FCC_ERR_UNSUPPORTED, "the split form is FP32 only");
     if (d->K < 0) return fail(FCC_ERR_INVALID_ARG, "K < 0");
     const double c = d->c > 0 ? d->c : 343.0;
     int L;
@@ -231,6 +234,7 @@ fcc_status_t fcc::plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t 
     in.I = I;
     in.center = L * d->lag_den;
     in.prec = d->prec;
+    in.form = d->form;
     in.delta = 1.0 / d->lag_den;
     in.fs = d->fs;
     in.c = c;
@@ -307,10 +311,24 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
         return st;
     }
     const int kmax = std::max(in.K_even, in.K_odd);
-    p->kh = kmax <= 2 ? 2 : kmax <= 4 ? 4 : kmax <= 6 ? 6 : kmax <= 8 ? 8 : 0;
+    if (in.form == FCC_FORM_REIM_SPLIT) {
+        // KB = max(K_c, K_s) packed coefficient pairs (c_k, s_k), rounded up to a
+        // multiple of 4; the per-pair kernel's template counts KB / 2 of them
+        const int kb = (kmax + 3) / 4 * 4;
+        p->kh = kb <= 16 ? kb / 2 : 0;
+    } else {
+        p->kh = kmax <= 2 ? 2 : kmax <= 4 ? 4 : kmax <= 6 ? 6 : kmax <= 8 ? 8 : 0;
+    }
     std::vector<Slot> slots = make_slots(in.M);
     p->n_slots = (int)slots.size();
-    if (p->kh) {
+    if (in.form == FCC_FORM_REIM_SPLIT) {
+        st = set_fp32_geometry(p, Fp32Geometry{});  // placeholder tables: the folded kernel is not used
+        if (st == FCC_OK && p->kh) st = prepare_reim(p);
+        if (st != FCC_OK) {
+            free_plan(p);
+            return st;
+        }
+    } else if (p->kh) {
         st = choose_fp32_geometry(p);
         if (st == FCC_OK) st = set_fp32_geometry(p, p->geo);
         if (st != FCC_OK) {

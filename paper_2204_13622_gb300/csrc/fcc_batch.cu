@@ -158,6 +158,8 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
     for (int a = 0; a < n_arrays; ++a) {
         if (descs[a].prec != FCC_PREC_FP32)
             return fail(FCC_ERR_INVALID_ARG, "array " + std::to_string(a) + ": the batched form is FP32");
+        if (descs[a].form != FCC_FORM_FOLDED)
+            return fail(FCC_ERR_UNSUPPORTED, "array " + std::to_string(a) + ": the batched form is the folded one");
         if (T[a] < 1) return fail(FCC_ERR_INVALID_ARG, "array " + std::to_string(a) + ": T < 1");
     }
     fcc_batch *b = new (std::nothrow) fcc_batch();

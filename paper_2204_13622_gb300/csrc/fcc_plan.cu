@@ -56,6 +56,19 @@ __global__ void build_halves_kernel(int I, int Ld, int den, int N, int Q, double
     if (f < Q) Ao[(size_t)i * Q + f] = r2 * s;
 }
 
+// The split form's matrices C = Re W and S = Im W (Eq. 3), [I][N/2 + 1]:
+// 2 pi f tau_i / N = pi * 2 f (i - L den) / (den N).
+__global__ void build_reim_kernel(int I, int Ld, int den, int N, int B, double *Ac, double *As)
+{
+    int i = blockIdx.y;
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I || f >= B) return;
+    double s, c;
+    sincospi_ratio(2LL * f * ((long long)i - Ld), (long long)den * N, &s, &c);
+    Ac[(size_t)i * B + f] = c;
+    As[(size_t)i * B + f] = s;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -169,8 +182,10 @@ void launch_basis_kernels(const fcc_plan_info_t &in, double *d_Ae, double *d_Ao,
 struct BasisKey {
     int dev, N, I, den, K_req;
     double energy;
+    int form;
     bool operator<(const BasisKey &o) const
     {
+        if (form != o.form) return form < o.form;
         if (dev != o.dev) return dev < o.dev;
         if (N != o.N) return N < o.N;
         if (I != o.I) return I < o.I;
@@ -191,7 +206,7 @@ static fcc_status_t build_plan_bases_uncached(fcc_plan *plan, int K_req, double 
 fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
 {
     fcc_plan_info_t &in = plan->info;
-    const BasisKey key{plan->device, in.N, in.I, in.den, K_req > 0 ? K_req : 0, K_req > 0 ? 0.0 : energy};
+    const BasisKey key{plan->device, in.N, in.I, in.den, K_req > 0 ? K_req : 0, K_req > 0 ? 0.0 : energy, in.form};
     {
         std::lock_guard<std::mutex> lk(g_basis_mu);
         auto it = g_basis_cache.find(key);
@@ -217,9 +232,12 @@ fcc_status_t build_plan_bases(fcc_plan *plan, int K_req, double energy)
     return FCC_OK;
 }
 
+static fcc_status_t build_reim_bases(fcc_plan *plan, int K_req, double energy);
+
 static fcc_status_t build_plan_bases_uncached(fcc_plan *plan, int K_req, double energy)
 {
     fcc_plan_info_t &in = plan->info;
+    if (in.form == FCC_FORM_REIM_SPLIT) return build_reim_bases(plan, K_req, energy);
     const int I = in.I, Q = in.Q, nE = Q + 1, nO = Q;
     double *d_Ae = nullptr, *d_Ao = nullptr, *d_Je = nullptr, *d_Jo = nullptr;
     int *d_sw = nullptr;
@@ -343,6 +361,110 @@ fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, co
     return FCC_OK;
 }
 
+// The split form: C = Re W and S = Im W each get their own FP64 Jacobi SVD on
+// the GPU and their own rank (the energy rule on that matrix's singular values,
+// extended over ties, or K_req for both).  Kept vectors: projection rows
+// sigma_k v_k into Pe (C) / Po (S) over all N/2 + 1 bins, left vectors u_k into
+// Ue / Uo, with the canonical sign of the folded form.
+static fcc_status_t build_reim_bases(fcc_plan *plan, int K_req, double energy)
+{
+    fcc_plan_info_t &in = plan->info;
+    const int I = in.I, B = in.B;
+    double *d_A[2] = {nullptr, nullptr}, *d_J[2] = {nullptr, nullptr};
+    int *d_sw = nullptr;
+    auto cleanup = [&]() {
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(d_A[b]);
+            cudaFree(d_J[b]);
+        }
+        cudaFree(d_sw);
+    };
+    bool ok = cudaMalloc(&d_sw, 2 * sizeof(int)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaMalloc(&d_A[b], sizeof(double) * (size_t)I * B) == cudaSuccess &&
+             cudaMalloc(&d_J[b], sizeof(double) * (size_t)I * I) == cudaSuccess;
+    if (!ok) {
+        cleanup();
+        (void)cudaGetLastError();
+        return fail(FCC_ERR_OOM, "split-form plan workspace");
+    }
+    dim3 gb((B + 127) / 128, I);
+    build_reim_kernel<<<gb, 128>>>(I, in.L * in.den, in.den, in.N, B, d_A[0], d_A[1]);
+    const double tiny2 = 1e-30 * (double)I * (double)B;
+    jacobi_svd_kernel<<<2, kJacobiThreads>>>(JacobiJob{d_A[0], d_J[0], I, B, d_sw},
+                                            JacobiJob{d_A[1], d_J[1], I, B, d_sw + 1}, tiny2);
+    std::vector<double> X[2], J[2];
+    int sw[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    for (int b = 0; b < 2; ++b) {
+        X[b].resize((size_t)I * B);
+        J[b].resize((size_t)I * I);
+        if (e == cudaSuccess) e = cudaMemcpy(X[b].data(), d_A[b], sizeof(double) * X[b].size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(J[b].data(), d_J[b], sizeof(double) * J[b].size(), cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(sw, d_sw, sizeof(sw), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "split-form basis construction");
+    if (sw[0] < 0 || sw[1] < 0) return fail(FCC_ERR_NOT_CONVERGED, "Jacobi SVD did not converge");
+    int K[2];
+    std::vector<double> P[2], U[2];
+    for (int b = 0; b < 2; ++b) {
+        std::vector<double> sig(I);
+        std::vector<int> order(I);
+        for (int k = 0; k < I; ++k) {
+            double a = 0;
+            for (int t = 0; t < B; ++t) a += X[b][(size_t)k * B + t] * X[b][(size_t)k * B + t];
+            sig[k] = std::sqrt(a);
+            order[k] = k;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return sig[a] > sig[c]; });
+        std::vector<double> sorted(I);
+        double tot = 0;
+        for (int k = 0; k < I; ++k) {
+            sorted[k] = sig[order[k]];
+            tot += sorted[k] * sorted[k];
+        }
+        int Kb = K_req;
+        if (Kb <= 0) {
+            double acc = 0;
+            Kb = I;
+            for (int k = 0; k < I; ++k) {
+                acc += sorted[k] * sorted[k];
+                if (acc >= energy * tot) {
+                    Kb = k + 1;
+                    break;
+                }
+            }
+            while (Kb < I && sorted[Kb - 1] - sorted[Kb] <= 1e-12 * sorted[Kb - 1]) ++Kb;
+        }
+        if (Kb > I || sorted[Kb - 1] <= 1e-12 * sorted[0])
+            return fail(FCC_ERR_INVALID_ARG, "K exceeds the numerical rank of the cosine or sine matrix");
+        K[b] = Kb;
+        sorted.resize(std::min(I, B));
+        (b == 0 ? plan->s_even : plan->s_odd) = sorted;
+        P[b].assign((size_t)Kb * B, 0.0);
+        U[b].assign((size_t)I * Kb, 0.0);
+        for (int k = 0; k < Kb; ++k) {
+            const double *y = &X[b][(size_t)order[k] * B];
+            const double *u = &J[b][(size_t)order[k] * I];
+            int am = 0;
+            for (int t = 1; t < B; ++t)
+                if (std::fabs(y[t]) > std::fabs(y[am])) am = t;
+            const double sg = y[am] < 0 ? -1.0 : 1.0;
+            for (int t = 0; t < B; ++t) P[b][(size_t)k * B + t] = sg * y[t];
+            for (int i = 0; i < I; ++i) U[b][(size_t)i * Kb + k] = sg * u[i];
+        }
+    }
+    in.K_even = K[0];
+    in.K_odd = K[1];
+    in.K = K[0] + K[1];
+    plan->Pe = P[0];
+    plan->Po = P[1];
+    plan->Ue = U[0];
+    plan->Uo = U[1];
+    return FCC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free basis construction (fcc_plan_bases_noalloc).  The working
 // matrices of the two Jacobi SVDs live in one static device array instead of
@@ -389,6 +511,7 @@ extern "C" fcc_status_t fcc_plan_bases_noalloc(const fcc_plan_desc_t *desc, fcc_
     int dev = 0;
     fcc_status_t st = plan_info_from_desc(desc, tmp.info, dev);
     if (st != FCC_OK) return st;
+    if (tmp.info.form != FCC_FORM_FOLDED) return fail(FCC_ERR_UNSUPPORTED, "the allocation-free build is for the folded form");
     const fcc_plan_info_t &in = tmp.info;
     const size_t I = in.I, Q = in.Q;
     const size_t need = kNoAllocHeader + I * (2 * Q + 1) + 2 * I * I;

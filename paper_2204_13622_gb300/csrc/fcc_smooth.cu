@@ -129,15 +129,18 @@ __global__ void carry_kernel(float2 *sums_to_carry, int PB, int n_chunks, long l
 // different 16-byte bank groups), then the pairs' 2 KH coefficients, then the
 // four pairs' smoothed R at the lone bin N/4.
 struct SmoothLayout {
-    int QP, row_bytes, warp_bytes;
+    int QP, rows, row_bytes, warp_bytes;
     size_t basis_off, recon_off, warps_off, stages_off, stage_bytes, total;
-    __host__ __device__ SmoothLayout(int Q, int KH, int center, int M, int B, int n_warps)
+    __host__ __device__ SmoothLayout(int Q, int KH, int center, int M, int B, int n_warps, bool FB)
     {
-        QP = (Q + 4) & ~3;
+        // folded form: 8 rows (x_s, x_d of 4 pairs) of records 0..Q; split form:
+        // 4 rows (R_hat of 4 pairs) of bins 0..2Q, whose weights stay in global memory
+        QP = FB ? (2 * Q + 4) : ((Q + 4) & ~3);
+        rows = FB ? 4 : 8;
         row_bytes = QP * 8 + 16;
-        warp_bytes = (8 * row_bytes + 4 * 2 * KH * 8 + 4 * 8 + 127) & ~127;
+        warp_bytes = (rows * row_bytes + 4 * 2 * KH * 8 + 4 * 8 + 127) & ~127;
         basis_off = 128 + 8 * sizeof(Slot);
-        recon_off = basis_off + (size_t)2 * KH * QP * 4;
+        recon_off = basis_off + (FB ? 0 : (size_t)2 * KH * QP * 4);
         warps_off = (recon_off + (size_t)(center + 1) * 4 * KH * 4 + 127) & ~(size_t)127;
         stages_off = warps_off + (size_t)n_warps * warp_bytes;
         stage_bytes = ((size_t)M * B * 8 + 127) & ~(size_t)127;
@@ -171,12 +174,16 @@ __device__ __forceinline__ f2 unit_scaled(float rx, float ry, bool &bad)
     return mul2(ab, pk(r, r));
 }
 
-template <int KH, int RS>
+// FB (the split form): the rows hold R_hat at bins 0..N/2 unfolded, the
+// projection pairs the cosine weight with Re and the sine weight with Im in one
+// FFMA2 ((c_k, s_k) per coefficient), and the reconstruction table holds
+// (2 U_c, 2 U_s) so the same S -/+ D evaluation gives y = 2 (U_c c - U_s s).
+template <int KH, int RS, bool FB>
 __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constant__ SmoothParams p)
 {
     constexpr int CPL = KH > 4 ? 2 : 1;  // coefficients per projecting lane
     extern __shared__ __align__(128) unsigned char smem[];
-    const SmoothLayout Ly(p.Q, KH, p.center, p.M, p.B, p.n_slots);
+    const SmoothLayout Ly(p.Q, KH, p.center, p.M, p.B, p.n_slots, FB);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
     uint64_t *freed = full + kSmoothStages;
     Slot *slots = reinterpret_cast<Slot *>(smem + 128);
@@ -197,18 +204,19 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
-    for (int e = threadIdx.x; e < 2 * KH * QP; e += blockDim.x) basis[e] = p.basis[e];
+    if (!FB)
+        for (int e = threadIdx.x; e < 2 * KH * QP; e += blockDim.x) basis[e] = p.basis[e];
     for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
     unsigned char *wreg = smem + Ly.warps_off + (size_t)warp * Ly.warp_bytes;
-    // the padding records Q + 1 .. QP - 1 stay zero (their basis entries are zero too)
-    const int npad = QP - Q - 1;
-    for (int e = lane; e < 8 * npad; e += 32)
-        reinterpret_cast<float2 *>(wreg + (size_t)(e / npad) * Ly.row_bytes)[Q + 1 + e % npad] = make_float2(0.f, 0.f);
+    // the padding entries past the last record (bin) stay zero (their weights are zero too)
+    const int used = FB ? 2 * Q + 1 : Q + 1, npad = QP - used;
+    for (int e = lane; e < Ly.rows * npad; e += 32)
+        reinterpret_cast<float2 *>(wreg + (size_t)(e / npad) * Ly.row_bytes)[used + e % npad] = make_float2(0.f, 0.f);
     fence_proxy_async();
     __syncthreads();
 
     const Slot sl = slots[warp];
-    float2 *zbuf = reinterpret_cast<float2 *>(wreg + 8 * Ly.row_bytes);  // [4][2 KH]
+    float2 *zbuf = reinterpret_cast<float2 *>(wreg + (size_t)Ly.rows * Ly.row_bytes);  // [4][2 KH]
     f2 *Rl = reinterpret_cast<f2 *>(zbuf + 4 * 2 * KH);                 // [4], lane 0's
     bool bad = false, failed = false;
     // This CTA's frames as one sequence g = i * chunk + k over its chunks
@@ -247,16 +255,17 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int pq = sl.pair[q] >= 0 ? sl.pair[q] : 0;
-            const float2 *cs = p.carry + ((size_t)c * p.P + pq) * B;
+            // no carry (alpha = 1): every chunk starts from R = 0
+            const float2 *cs = p.carry ? p.carry + ((size_t)c * p.P + pq) * B : nullptr;
 #pragma unroll
             for (int j = 0; j < RS; ++j) {
                 const int fp = lane + 32 * j;
-                const float2 u = cs[fp], v = cs[2 * Q - fp];
+                const float2 u = cs ? cs[fp] : make_float2(0.f, 0.f), v = cs ? cs[2 * Q - fp] : make_float2(0.f, 0.f);
                 R[q][j][0] = mul2(ia2, pk(u.x, u.y));
                 R[q][j][1] = mul2(ia2, pk(v.x, v.y));
             }
             if (lane == 0) {
-                const float2 w = cs[Q];
+                const float2 w = cs ? cs[Q] : make_float2(0.f, 0.f);
                 Rl[q] = mul2(ia2, pk(w.x, w.y));
             }
         }
@@ -305,8 +314,13 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                     upk(R[q][j][0], r0x, r0y);
                     upk(R[q][j][1], r1x, r1y);
                     const f2 ua = unit_scaled(r0x, r0y, bad), ub = unit_scaled(r1x, r1y, bad);
-                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[fp] = add2(ua, ub);
-                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[fp] = sub2(ua, ub);
+                    if (FB) {
+                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[fp] = ua;
+                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[2 * Q - fp] = ub;
+                    } else {
+                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[fp] = add2(ua, ub);
+                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[fp] = sub2(ua, ub);
+                    }
                 }
             }
             if (lane == 0) {
@@ -318,8 +332,12 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                     Rl[q] = fma2(beta2, Rl[q], a);
                     float rx, ry;
                     upk(Rl[q], rx, ry);
-                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
-                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[Q] = 0ull;
+                    if (FB) {
+                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
+                    } else {
+                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
+                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[Q] = 0ull;
+                    }
                 }
             }
             // the stage is read: release it (thread 0 refills it at the next frame)
@@ -329,7 +347,25 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
             // ---- project (Eqs. 7, 9): lane (q, i) forms coefficients v0 .. v0 + CPL - 1
             {
                 const int q = lane >> 3, v0 = (lane & 7) * CPL;
-                if (v0 < 2 * KH) {
+                if (FB && v0 < 2 * KH) {
+                    // (c_k, s_k) += (w_c, w_s) * (Re R_hat, Im R_hat), two bins per 16-byte load
+                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)q * Ly.row_bytes);
+                    f2 acc[CPL];
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0ull;
+#pragma unroll 4
+                    for (int r2 = 0; r2 < QP / 2; ++r2) {
+                        const float4 d = dat[r2];
+#pragma unroll
+                        for (int cc = 0; cc < CPL; ++cc) {
+                            const float4 w = __ldg(reinterpret_cast<const float4 *>(p.basis) + (size_t)(v0 + cc) * (QP / 2) + r2);
+                            acc[cc] = fma2(pk(w.x, w.y), pk(d.x, d.y), acc[cc]);
+                            acc[cc] = fma2(pk(w.z, w.w), pk(d.z, d.w), acc[cc]);
+                        }
+                    }
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + v0 + cc] = acc[cc];
+                } else if (!FB && v0 < 2 * KH) {
                     const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * q + (v0 >= KH)) * Ly.row_bytes);
                     f2 acc[CPL];
 #pragma unroll
@@ -404,7 +440,7 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                     }
                     p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
                 }
-                if (p.out_coef) {
+                if (!FB && p.out_coef) {
                     const int K = p.KE + p.KO;
                     float *cf = p.out_coef + o * 2 * K;
 #pragma unroll
@@ -448,53 +484,190 @@ struct SmoothPlan {
     size_t smem, work_bytes;
 };
 
+bool is_split(const fcc_plan *plan) { return plan->info.form == FCC_FORM_REIM_SPLIT; }
+
 fcc_status_t smooth_geometry(const fcc_plan *plan, long long T, SmoothPlan &g)
 {
     const fcc_plan_info_t &in = plan->info;
-    if (in.prec != FCC_PREC_FP32) return fail(FCC_ERR_UNSUPPORTED, "the smoothed path is FP32");
-    if (in.M % 2) return fail(FCC_ERR_UNSUPPORTED, "the smoothed path needs an even number of mics");
-    if (plan->n_slots > 8) return fail(FCC_ERR_UNSUPPORTED, "the smoothed path needs at most 8 mics");
-    if (in.Q < 32 || in.Q > 128) return fail(FCC_ERR_UNSUPPORTED, "the smoothed path needs 128 <= N <= 512");
-    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
+    const char *what = is_split(plan) ? "the split form" : "the smoothed path";
+    if (in.prec != FCC_PREC_FP32) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " is FP32");
+    if (in.M % 2) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " needs an even number of mics");
+    if (plan->n_slots > 8) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " needs at most 8 mics");
+    if (in.Q < 32 || in.Q > 128) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " needs 128 <= N <= 512");
+    if (!plan->kh) return fail(FCC_ERR_UNSUPPORTED, "too many bases for the per-pair kernel");
     const long long target = 4LL * plan->num_sms;
     g.chunk = (int)std::max<long long>(64, (T + target - 1) / target);
     g.n_chunks = (int)((T + g.chunk - 1) / g.chunk);
     g.threads = 32 * plan->n_slots;
-    const SmoothLayout Ly(in.Q, plan->kh, in.center, in.M, in.B, plan->n_slots);
+    const SmoothLayout Ly(in.Q, plan->kh, in.center, in.M, in.B, plan->n_slots, is_split(plan));
     g.smem = Ly.total;
     g.work_bytes = (size_t)g.n_chunks * in.P * in.B * sizeof(float2);
     return FCC_OK;
 }
 
 // grid = min(chunks, resident CTAs): the CTAs are persistent over chunks
-template <int KH, int RS>
+template <int KH, int RS, bool FB>
 fcc_status_t launch_smooth_inst(const SmoothParams &prm, int num_sms, int threads, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(fcc_smooth_kernel<KH, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fcc_smooth_kernel<KH, RS, FB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fcc_smooth_kernel)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fcc_smooth_kernel<KH, RS>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fcc_smooth_kernel<KH, RS, FB>, threads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) return fail(FCC_ERR_UNSUPPORTED, "the smoothed kernel does not fit an SM");
+    if (per_sm < 1) return fail(FCC_ERR_UNSUPPORTED, "the per-pair kernel does not fit an SM");
     const int grid = (int)std::min<long long>(prm.n_chunks, (long long)num_sms * per_sm);
-    fcc_smooth_kernel<KH, RS><<<grid, threads, smem, st>>>(prm);
+    fcc_smooth_kernel<KH, RS, FB><<<grid, threads, smem, st>>>(prm);
     e = cudaGetLastError();
     return e == cudaSuccess ? FCC_OK : cuda_fail(e, "fcc_smooth_kernel launch");
 }
 
-template <int KH>
+template <int KH, bool FB>
 fcc_status_t launch_smooth_kh(int rs, const SmoothParams &prm, int num_sms, int threads, size_t smem, cudaStream_t st)
 {
     switch (rs) {
-    case 1: return launch_smooth_inst<KH, 1>(prm, num_sms, threads, smem, st);
-    case 2: return launch_smooth_inst<KH, 2>(prm, num_sms, threads, smem, st);
-    case 4: return launch_smooth_inst<KH, 4>(prm, num_sms, threads, smem, st);
-    default: return fail(FCC_ERR_UNSUPPORTED, "the smoothed path needs 128 <= N <= 512");
+    case 1: return launch_smooth_inst<KH, 1, FB>(prm, num_sms, threads, smem, st);
+    case 2: return launch_smooth_inst<KH, 2, FB>(prm, num_sms, threads, smem, st);
+    case 4: return launch_smooth_inst<KH, 4, FB>(prm, num_sms, threads, smem, st);
+    default: return fail(FCC_ERR_UNSUPPORTED, "the per-pair kernel needs 128 <= N <= 512");
     }
 }
 
+template <bool FB>
+fcc_status_t launch_smooth_form(int kh, int rs, const SmoothParams &prm, int num_sms, int threads, size_t smem,
+                                cudaStream_t st)
+{
+    switch (kh) {
+    case 2: return launch_smooth_kh<2, FB>(rs, prm, num_sms, threads, smem, st);
+    case 4: return launch_smooth_kh<4, FB>(rs, prm, num_sms, threads, smem, st);
+    case 6: return launch_smooth_kh<6, FB>(rs, prm, num_sms, threads, smem, st);
+    case 8: return launch_smooth_kh<8, FB>(rs, prm, num_sms, threads, smem, st);
+    default: return fail(FCC_ERR_UNSUPPORTED, "too many bases for the per-pair kernel");
+    }
+}
+
+// Folded-form weights in the per-pair kernel's layout: row v < KH = even basis v
+// over records 0..Q, row KH + v = odd basis v (zero at Q); padding records zero.
+fcc_status_t folded_weights(fcc_plan *plan)
+{
+    if (plan->d_smooth_basis) return FCC_OK;
+    const fcc_plan_info_t &in = plan->info;
+    const int kh = plan->kh, Q = in.Q;
+    const SmoothLayout Ly(Q, kh, in.center, in.M, in.B, plan->n_slots, false);
+    std::vector<float> bas((size_t)2 * kh * Ly.QP, 0.f);
+    for (int k = 0; k < in.K_even; ++k)
+        for (int f = 0; f <= Q; ++f) bas[(size_t)k * Ly.QP + f] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
+    for (int k = 0; k < in.K_odd; ++k)
+        for (int f = 0; f < Q; ++f) bas[(size_t)(kh + k) * Ly.QP + f] = (float)plan->Po[(size_t)k * Q + f];
+    float *d = nullptr;
+    FCC_CUDA_TRY(dev_alloc((void **)&d, bas.size() * sizeof(float)));
+    cudaError_t e = cudaMemcpy(d, bas.data(), bas.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(per-pair weights)");
+    }
+    plan->d_smooth_basis = d;
+    return FCC_OK;
+}
+
+// The per-pair kernel over T frames: `carry` (may be null: every chunk starts
+// from R = 0, which is exact for alpha = 1) holds the state entering each chunk.
+fcc_status_t run_per_pair(const fcc_plan *plan, const SmoothPlan &g, const float2 *spectra, long long T, float a,
+                          float b, const float2 *carry, int *idx, float *peak, float *tau, float *coef, cudaStream_t s)
+{
+    const fcc_plan_info_t &in = plan->info;
+    SmoothParams prm{};
+    prm.spectra = spectra;
+    prm.T = T;
+    prm.M = in.M;
+    prm.B = in.B;
+    prm.Q = in.Q;
+    prm.P = in.P;
+    prm.n_slots = plan->n_slots;
+    prm.chunk = g.chunk;
+    prm.n_chunks = g.n_chunks;
+    prm.alpha = a;
+    prm.beta = b;
+    prm.carry = carry;
+    prm.basis = plan->d_smooth_basis;
+    prm.recon = plan->d_recon;
+    prm.slots = plan->d_slots;
+    prm.center = in.center;
+    prm.I = in.I;
+    prm.KE = in.K_even;
+    prm.KO = in.K_odd;
+    prm.delta = (float)in.delta;
+    prm.out_idx = idx;
+    prm.out_peak = peak;
+    prm.out_tau = tau;
+    prm.out_coef = coef;
+    prm.err = plan->d_err;
+    prm.wait_cycles = debug_hooks().wait_cycles;
+    const int rs = in.Q / 32;
+    return is_split(plan) ? launch_smooth_form<true>(plan->kh, rs, prm, plan->num_sms, g.threads, g.smem, s)
+                          : launch_smooth_form<false>(plan->kh, rs, prm, plan->num_sms, g.threads, g.smem, s);
+}
+
 }  // namespace
+
+// Split-form tables for the per-pair kernel, built once when the plan is
+// created: weights [2 KH][2Q + 4] of (cosine, sine) pairs (sigma v_k of C and
+// of S over bins 0..N/2, zero past K_c / K_s and in the padding), and the
+// reconstruction table [center + 1][KH][4] = (2 U_c[k], 2 U_s[k], 2 U_c[KH + k],
+// 2 U_s[KH + k]) at tau = +m / den, which replaces the folded table.
+fcc_status_t prepare_reim(fcc_plan *plan)
+{
+    const fcc_plan_info_t &in = plan->info;
+    const int kh = plan->kh, B = in.B, Kc = in.K_even, Ks = in.K_odd, I = in.I;
+    const SmoothLayout Ly(in.Q, kh, in.center, in.M, in.B, std::max(plan->n_slots, 1), true);
+    std::vector<float> w((size_t)2 * kh * Ly.QP * 2, 0.f);
+    for (int k = 0; k < 2 * kh; ++k)
+        for (int f = 0; f < B; ++f) {
+            w[((size_t)k * Ly.QP + f) * 2] = k < Kc ? (float)plan->Pe[(size_t)k * B + f] : 0.f;
+            w[((size_t)k * Ly.QP + f) * 2 + 1] = k < Ks ? (float)plan->Po[(size_t)k * B + f] : 0.f;
+        }
+    std::vector<float> rec((size_t)(in.center + 1) * 4 * kh, 0.f);
+    auto uc = [&](int i, int k) { return k < Kc ? plan->Ue[(size_t)i * Kc + k] : 0.0; };
+    auto us = [&](int i, int k) { return k < Ks ? plan->Uo[(size_t)i * Ks + k] : 0.0; };
+    for (int m = 0; m <= in.center; ++m) {
+        const int i = in.center + m;
+        (void)I;
+        for (int k = 0; k < kh; ++k) {
+            float *g = &rec[((size_t)m * kh + k) * 4];
+            g[0] = (float)(2.0 * uc(i, k));
+            g[1] = (float)(2.0 * us(i, k));
+            g[2] = (float)(2.0 * uc(i, kh + k));
+            g[3] = (float)(2.0 * us(i, kh + k));
+        }
+    }
+    float *dw = nullptr, *dr = nullptr;
+    cudaError_t e = dev_alloc((void **)&dw, w.size() * sizeof(float));
+    if (e == cudaSuccess) e = dev_alloc((void **)&dr, rec.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dr, rec.data(), rec.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dw);
+        cudaFree(dr);
+        return cuda_fail(e, "split-form tables");
+    }
+    cudaFree(plan->d_smooth_basis);
+    cudaFree(plan->d_recon);
+    plan->d_smooth_basis = dw;
+    plan->d_recon = dr;
+    return FCC_OK;
+}
+
+fcc_status_t launch_reim(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak, float *tau,
+                         float *coef, float *corr, cudaStream_t st)
+{
+    if (coef || corr) return fail(FCC_ERR_UNSUPPORTED, "the split form has no coefficient or correlation output");
+    SmoothPlan g{};
+    fcc_status_t s = smooth_geometry(plan, std::max<long long>(T, 1), g);
+    if (s != FCC_OK) return s;
+    if (T == 0) return FCC_OK;
+    return run_per_pair(plan, g, spectra, T, 1.f, 0.f, nullptr, idx, peak, tau, nullptr, st);
+}
+
 }  // namespace fcc
 
 using namespace fcc;
@@ -524,6 +697,7 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
     if (st != FCC_OK) return st;
     if (T == 0) return FCC_OK;
     if (!d_spectra || !d_lag_idx || !d_peak || !d_work) return fail(FCC_ERR_INVALID_ARG, "null spectra/outputs/work");
+    if (d_coeffs && is_split(plan)) return fail(FCC_ERR_UNSUPPORTED, "the split form has no coefficient output");
     if (reinterpret_cast<uintptr_t>(d_spectra) & 15) return fail(FCC_ERR_INVALID_ARG, "spectra not 16-byte aligned");
     if ((reinterpret_cast<uintptr_t>(d_state) | reinterpret_cast<uintptr_t>(d_work)) & 7)
         return fail(FCC_ERR_INVALID_ARG, "state / workspace not 8-byte aligned");
@@ -552,56 +726,12 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "smoothing carry kernels");
     }
-    // basis in the smoothed kernel's layout: row v < KH = even basis v over
-    // records 0..Q, row KH + v = odd basis v (zero at Q); padding records zero
-    if (!plan->d_smooth_basis) {
-        const int kh = plan->kh, Q = in.Q;
-        const SmoothLayout Ly(Q, kh, in.center, in.M, in.B, plan->n_slots);
-        std::vector<float> bas((size_t)2 * kh * Ly.QP, 0.f);
-        for (int k = 0; k < in.K_even; ++k)
-            for (int f = 0; f <= Q; ++f) bas[(size_t)k * Ly.QP + f] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
-        for (int k = 0; k < in.K_odd; ++k)
-            for (int f = 0; f < Q; ++f) bas[(size_t)(kh + k) * Ly.QP + f] = (float)plan->Po[(size_t)k * Q + f];
-        float *d = nullptr;
-        FCC_CUDA_TRY(cudaMalloc(&d, bas.size() * sizeof(float)));
-        FCC_CUDA_TRY(cudaMemcpy(d, bas.data(), bas.size() * sizeof(float), cudaMemcpyHostToDevice));
-        const_cast<fcc_plan *>(plan)->d_smooth_basis = d;
+    if (!is_split(plan)) {
+        st = folded_weights(plan);
+        if (st != FCC_OK) return st;
     }
-    SmoothParams prm{};
-    prm.spectra = static_cast<const float2 *>(d_spectra);
-    prm.T = T;
-    prm.M = in.M;
-    prm.B = in.B;
-    prm.Q = in.Q;
-    prm.P = in.P;
-    prm.n_slots = plan->n_slots;
-    prm.chunk = g.chunk;
-    prm.n_chunks = g.n_chunks;
-    prm.alpha = a;
-    prm.beta = b;
-    prm.carry = work;
-    prm.basis = plan->d_smooth_basis;
-    prm.recon = plan->d_recon;
-    prm.slots = plan->d_slots;
-    prm.center = in.center;
-    prm.I = in.I;
-    prm.KE = in.K_even;
-    prm.KO = in.K_odd;
-    prm.delta = (float)in.delta;
-    prm.out_idx = d_lag_idx;
-    prm.out_peak = d_peak;
-    prm.out_tau = d_tau_hat;
-    prm.out_coef = d_coeffs;
-    prm.err = plan->d_err;
-    prm.wait_cycles = debug_hooks().wait_cycles;
-    const int rs = in.Q / 32;
-    switch (plan->kh) {
-    case 2: return launch_smooth_kh<2>(rs, prm, plan->num_sms, g.threads, g.smem, s);
-    case 4: return launch_smooth_kh<4>(rs, prm, plan->num_sms, g.threads, g.smem, s);
-    case 6: return launch_smooth_kh<6>(rs, prm, plan->num_sms, g.threads, g.smem, s);
-    case 8: return launch_smooth_kh<8>(rs, prm, plan->num_sms, g.threads, g.smem, s);
-    default: return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
-    }
+    return run_per_pair(plan, g, static_cast<const float2 *>(d_spectra), T, a, b, work, d_lag_idx, d_peak, d_tau_hat,
+                        d_coeffs, s);
 }
 
 }  // extern "C"

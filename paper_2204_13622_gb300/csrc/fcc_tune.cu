@@ -332,6 +332,7 @@ fcc_status_t fcc_plan_autotune(fcc_plan_t *plan, const char *cache_path, int for
                                double *us_per_frame)
 {
     if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (plan->info.form != FCC_FORM_FOLDED) return fail(FCC_ERR_UNSUPPORTED, "the tuner times the folded-form kernel");
     DeviceScope scope(plan->device);
     if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
     return tune_fp32(plan, tune_cache_path(cache_path), force != 0, max_candidates, us_per_frame);
