@@ -701,6 +701,71 @@ def doa_chunk(doa, T):
     return max(1, min(T, doa.workspace(T) // (p.P * (p.I + 2) * 4)))
 
 
+def run_split_form(args, rank, world, local):
+    """The split form (cosine bases on Re x, sine bases on Im x) on the 8-mic
+    circle: fcc_tdoa on a FCC_FORM_REIM_SPLIT plan, per-pair kernel, alpha = 1."""
+    import numpy as np
+    import torch
+
+    from paper_2204_13622_gb300 import binding, workloads
+    w = {"circle8": workloads.CIRCLE8, "square4": workloads.SQUARE4}[args.workload]
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    distributed = dist_init(world, "nccl")
+    T, P = (args.frames or w.T), w.P
+    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, form="reim")
+    out = plan.tdoa(X)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        plan.tdoa(X, out=out)
+    plan.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(distributed)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for k in range(args.steps):
+            plan.tdoa(X, out=out)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(distributed)
+    plan.sync()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = sum(per) / args.steps
+    ms_max = max_over_ranks(ms, distributed, dev)
+    res = None
+    if rank == 0:
+        from oracle import oracle as O
+        n = min(256, T)
+        ob = O.BasisB(w.N, w.L, w.lag_den)
+        t1 = time.perf_counter()
+        idx, _, _, _ = O.tdoa(X[:n].cpu().numpy(), ob.WK, ob.taus, ob.delta)
+        t_or = time.perf_counter() - t1
+        got = out["lag_idx"][:n].cpu().numpy()
+        B, K, center = w.N // 2 + 1, plan.K, (plan.I - 1) // 2
+        # per bin: cross spectrum 4, recursion update 2, phase transform 6; projection
+        # 2 per (coefficient, bin); reconstruction 2 K + 2 per lag step (FMA = 1)
+        ops = T * P * (12 * B + 2 * K * B + (center + 1) * (2 * K + 2))
+        bytes_alg = T * (w.M * w.B * 8) + T * P * 12
+        peak, psrc = _peak_hbm()
+        res = {"metric": METRIC, "value": whole_job_rate(T * P, world, ms_max / 1000.0), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": f"{w.name}, split form (cosine / sine bases)", "frames": T, "pairs": P,
+                          "K_c": plan.K_even, "K_s": plan.K_odd, "l2": "inputs larger than L2; no flush"},
+               "roofline": dict(alu_roofline(ops, ms, "fcc_smooth_kernel (split form, alpha = 1)"), traffic=None,
+                                hbm={"achieved": bytes_alg / (ms / 1000.0) / 1e9, "peak": peak,
+                                     "frac": bytes_alg / (ms / 1000.0) / 1e9 / peak, "peak_source": psrc}),
+               "accuracy_vs_oracle": {"pair_frames": int(got.size), "argmax_agreement": float((got == idx).mean())},
+               "cpu_baseline": {"value": n * P / t_or, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                                "sample": f"first {n} frames, FP64 form B"},
+               "gpu_launches": args.steps, "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
+    plan.close()
+    return res
+
+
 def run_smoothed(args, rank, world, local):
     """Eq. 1 with alpha < 1 on a single-array workload: chunk sums, carry scan and
     the FCC pass per step, the stream state carried from step to step."""
@@ -714,7 +779,7 @@ def run_smoothed(args, rank, world, local):
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
     X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
-    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local)
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, form=args.form)
     state = torch.zeros((P, w.B), dtype=torch.complex64, device=dev)
     work = torch.empty(max(plan.smooth_workspace(T), 8), dtype=torch.uint8, device=dev)
     out = plan.tdoa_smoothed(X, args.alpha, state=state, work=work)
@@ -746,7 +811,7 @@ def run_smoothed(args, rank, world, local):
         st0 = torch.zeros_like(state)
         o2 = plan.tdoa_smoothed(X[:n].contiguous(), args.alpha, state=st0)
         plan.sync()
-        basis = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+        basis = O.Basis(w.N, w.L, w.lag_den, K=plan.K) if args.form == "folded" else O.BasisB(w.N, w.L, w.lag_den)
         t1 = time.perf_counter()
         idx, pk_, _, y, _ = O.tdoa_smoothed(X[:n].cpu().numpy(), basis.WK, basis.taus, basis.delta, args.alpha,
                                            want_y=True)
@@ -756,7 +821,8 @@ def run_smoothed(args, rank, world, local):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": {"workload": f"{w.name}, Eq. 1 smoothing alpha={args.alpha}", "frames": T, "pairs": P,
+               "config": {"workload": f"{w.name}, Eq. 1 smoothing alpha={args.alpha}"
+                                      + (", split form" if args.form == "reim" else ""), "frames": T, "pairs": P,
                           "state": "carried from step to step",
                           "l2": "inputs larger than L2; no flush"},
                "roofline": dict(alu_roofline(T * P * smooth_ops_per_pair_frame(w.M, w.N, plan.K_even, plan.K_odd, plan.I),
@@ -866,6 +932,8 @@ def main(argv=None):
                     help="Eq. 1 smoothing factor; < 1 times the smoothed path (FCC leg only)")
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
     ap.add_argument("--dirs", type=int, default=1024, help="doa: candidate directions (hemisphere)")
+    ap.add_argument("--form", default="folded", choices=["folded", "reim"],
+                    help="basis split: the paper's folded form, or cosine/sine bases on Re/Im")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batched: keep the heuristic tile shapes (default: autotuned)")
     ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")
@@ -880,6 +948,8 @@ def main(argv=None):
         g.build() if rank == 0 and world == 1 else None
         if args.alpha < 1.0:
             res = run_smoothed(args, rank, world, local)
+        elif args.form == "reim":
+            res = run_split_form(args, rank, world, local)
         elif args.workload == "batched":
             res = run_batched(args, rank, world, local)
         elif args.workload == "learned":
