@@ -766,6 +766,107 @@ def run_split_form(args, rank, world, local):
     return res
 
 
+def run_table1(args, rank, world, local):
+    """Synthetic reproduction of the Table 1 accuracy sweep: two microphones
+    d apart (d = 0.05 .. 0.15 m) in shoebox rooms made like the paper's (5-15 m
+    by 5-15 m by 3-4 m, absorption 0.2-0.8, source 1-5 m away, c 335-350 m/s,
+    white noise through image-source RIRs), STFT (N 512, hop 256) by the
+    library's front-end, then FCC with K = 1..8 on the grid step 1/2 (Eq. 1
+    smoothing alpha = 0.1, parabolic refinement) and GCC-PHAT with r = 1, 2, 4
+    on the same smoothed cross-spectrum; MAE of theta = arccos(tau c / (d fs))
+    in degrees against the geometric TDoA."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2204_13622_gb300 import binding, synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    FS, N, HOP, L, ALPHA, SIG, TRIR = 16000.0, 512, 256, 8, 0.1, 16000, 0.5
+    rng = np.random.default_rng(2022 + rank)
+    gen = torch.Generator(device=dev).manual_seed(2022 + rank)
+    ds = [round(0.05 + 0.01 * i, 2) for i in range(11)]
+    fcc = {k: binding.Plan(2, FS, N, 2, tau_max=L, K=k, device=local) for k in range(1, 9)}
+    gcc = {r: binding.Plan(2, FS, N, r, tau_max=L, device=local) for r in (1, 2, 4)}
+    names = [f"GCC r={r}" for r in (1, 2, 4)] + [f"FCC K={k}" for k in range(1, 9)]
+    err = {nm: [[] for _ in ds] for nm in names}
+
+    def unit(v):
+        return v / np.linalg.norm(v)
+
+    def parabola(y, i):
+        """Three-point refinement of the peak at index i (none at the ends or
+        when the points are not concave; offset clamped to +-1/2)."""
+        if i <= 0 or i >= len(y) - 1:
+            return 0.0
+        den = y[i - 1] - 2 * y[i] + y[i + 1]
+        return float(np.clip(0.5 * (y[i - 1] - y[i + 1]) / den, -0.5, 0.5)) if den < 0 else 0.0
+
+    t0 = time.perf_counter()
+    launches = 0
+    for di, d in enumerate(ds):
+        for _ in range(args.rooms):
+            room = np.array([rng.uniform(5, 15), rng.uniform(5, 15), rng.uniform(3, 4)])
+            beta = math.sqrt(1.0 - rng.uniform(0.2, 0.8))
+            c = rng.uniform(335.0, 350.0)
+            while True:
+                center = rng.uniform(0.5, room - 0.5)
+                axis = unit(rng.standard_normal(3))
+                dd = d + rng.uniform(-0.001, 0.001)
+                mics = np.stack([center + 0.5 * dd * axis, center - 0.5 * dd * axis])
+                src = center + rng.uniform(1.0, 5.0) * unit(rng.standard_normal(3))
+                if np.all(src > 0.3) and np.all(src < room - 0.3):
+                    break
+            h = synth.image_source_rir(room, src, mics, beta, FS, c, TRIR, device=dev)  # [2, n]
+            nr = h.shape[1]
+            noise = torch.randn(nr + SIG, generator=gen, device=dev)
+            nf = 1 << int(math.ceil(math.log2(2 * nr + SIG)))
+            x = torch.fft.irfft(torch.fft.rfft(noise, nf)[None] * torch.fft.rfft(h, nf), nf)[:, nr:nr + SIG]
+            pcm = (x / x.abs().max()).T.contiguous()
+            X = fcc[1].stft(pcm, HOP)
+            tau_true = (np.linalg.norm(src - mics[0]) - np.linalg.norm(src - mics[1])) * FS / c
+            th_true = math.degrees(math.acos(max(-1.0, min(1.0, tau_true * c / (dd * FS)))))
+            for k, plan in fcc.items():
+                o = plan.tdoa_smoothed(X, ALPHA)
+                tau = o["tau_hat"][:, 0].double().cpu().numpy()
+                th = np.degrees(np.arccos(np.clip(tau * c / (dd * FS), -1.0, 1.0)))
+                err[f"FCC K={k}"][di].append(np.abs(th - th_true))
+            # GCC on the smoothed cross-spectrum R: spectra (R, 1) give R_hat through the
+            # baseline's own phase transform
+            R = torch.zeros(X.shape[2], dtype=torch.complex64, device=dev)
+            Y = torch.ones((X.shape[0], 2, X.shape[2]), dtype=torch.complex64, device=dev)
+            for t in range(X.shape[0]):
+                R = (1 - ALPHA) * R + ALPHA * X[t, 0] * X[t, 1].conj()
+                Y[t, 0] = R
+            for r, plan in gcc.items():
+                g = plan.gcc_tdoa(Y, corr=True)
+                yc = g["corr"][:, 0].double().cpu().numpy()
+                idx = g["lag_idx"][:, 0].cpu().numpy()
+                tau = np.array([(i - L * r + parabola(yc[t], i)) / r for t, i in enumerate(idx)])
+                th = np.degrees(np.arccos(np.clip(tau * c / (dd * FS), -1.0, 1.0)))
+                err[f"GCC r={r}"][di].append(np.abs(th - th_true))
+            launches += 1 + 3 * len(fcc) + 3 * len(gcc)
+    for p in list(fcc.values()) + list(gcc.values()):
+        p.sync()
+        p.close()
+    mae = {nm: [float(np.concatenate(e).mean()) for e in err[nm]] for nm in names}
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_table1.json")))
+    res = None
+    if rank == 0:
+        res = {"metric": "TDoA mean absolute error (degrees), synthetic Table 1 sweep", "value":
+               float(np.mean(mae["FCC K=8"])), "unit": "degrees (FCC K=8, mean over d)", "n_gpus": world,
+               "steps": 1, "warmup": 0, "ms_per_step": 1000 * (time.perf_counter() - t0),
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (image-source rooms standing in for BIRD)",
+               "config": {"workload": "Table 1 sweep: 2 mics, d = 0.05..0.15 m, N 512, hop 256, alpha 0.1, "
+                                      "tau_max 8, FCC grid step 1/2, GCC r = 1, 2, 4",
+                          "rooms_per_d": args.rooms, "frames_per_room": int(X.shape[0]), "rir_s": TRIR},
+               "d_m": ds, "mae_deg": mae, "paper_mae_deg": gold["mae_deg"],
+               "gpu_launches": launches}
+    return res
+
+
 def run_smoothed(args, rank, world, local):
     """Eq. 1 with alpha < 1 on a single-array workload: chunk sums, carry scan and
     the FCC pass per step, the stream state carried from step to step."""
@@ -926,12 +1027,13 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=0, help="override the frame count (profiling)")
     ap.add_argument("--only", default="all", choices=["all", "fcc"], help="fcc: skip GCC, e2e, CPU legs")
     ap.add_argument("--workload", default="circle8",
-                    choices=["circle8", "grid16", "square4", "batched", "learned", "doa", "pcm"])
+                    choices=["circle8", "grid16", "square4", "batched", "learned", "doa", "pcm", "table1"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="Eq. 1 smoothing factor; < 1 times the smoothed path (FCC leg only)")
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
     ap.add_argument("--dirs", type=int, default=1024, help="doa: candidate directions (hemisphere)")
+    ap.add_argument("--rooms", type=int, default=24, help="table1: simulated rooms per microphone spacing")
     ap.add_argument("--form", default="folded", choices=["folded", "reim"],
                     help="basis split: the paper's folded form, or cosine/sine bases on Re/Im")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -958,6 +1060,8 @@ def main(argv=None):
             res = run_doa(args, rank, world, local)
         elif args.workload == "pcm":
             res = run_pcm(args, rank, world, local)
+        elif args.workload == "table1":
+            res = run_table1(args, rank, world, local) if rank == 0 else None
         else:
             res = run_fcc(args, rank, world, local)
     if res is not None:

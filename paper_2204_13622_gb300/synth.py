@@ -111,6 +111,49 @@ def pcm_far_field(n_samples: int, xyz: np.ndarray, fs: float, seed: int, device=
     return out
 
 
+def image_source_rir(room, src, mics, beta: float, fs: float, c: float, t_max: float, taps: int = 32,
+                     device="cpu"):
+    """Room impulse responses of a shoebox room by the image-source method
+    (Allen and Berkley, 1979): every image of the source in the six walls whose
+    delay is below t_max, with amplitude beta^(number of wall reflections) /
+    (4 pi r) (one reflection coefficient for all walls), placed at its
+    fractional delay r fs / c by a Hann-windowed sinc of 2 taps + 1 samples.
+    room [3] (m, corner at the origin), src [3], mics [M, 3].  Returns [M, n]
+    float32 (torch, on `device`), n = ceil(t_max fs) + taps + 1."""
+    import torch
+    room = np.asarray(room, np.float64)
+    src = np.asarray(src, np.float64)
+    mics = np.asarray(mics, np.float64).reshape(-1, 3)
+    n_out = int(math.ceil(t_max * fs)) + taps + 1
+    reach = c * t_max
+    axes = []
+    for a in range(3):
+        nmax = int(math.ceil(reach / (2 * room[a]))) + 1
+        n = np.arange(-nmax, nmax + 1)
+        pos = np.concatenate([src[a] + 2 * n * room[a], -src[a] + 2 * n * room[a]])
+        refl = np.concatenate([np.abs(n) + np.abs(n), np.abs(n - 1) + np.abs(n)])
+        axes.append((torch.tensor(pos, device=device), torch.tensor(refl, device=device)))
+    (px, rx), (py, ry), (pz, rz) = axes
+    order = (rx[:, None, None] + ry[None, :, None] + rz[None, None, :]).reshape(-1).double()
+    out = torch.zeros((mics.shape[0], n_out), dtype=torch.float64, device=device)
+    k = torch.arange(-taps, taps + 1, device=device, dtype=torch.float64)
+    for m in range(mics.shape[0]):
+        d2 = ((px - mics[m, 0]) ** 2)[:, None, None] + ((py - mics[m, 1]) ** 2)[None, :, None] \
+            + ((pz - mics[m, 2]) ** 2)[None, None, :]
+        dist = torch.sqrt(d2.reshape(-1))
+        keep = dist < reach
+        dist, o = dist[keep], order[keep]
+        amp = torch.pow(torch.tensor(beta, dtype=torch.float64, device=device), o) / (4 * math.pi * dist)
+        delay = dist * fs / c
+        base = torch.floor(delay)
+        idx = base[:, None] + k[None, :]
+        x = idx - delay[:, None]  # distance of each tap to the image's delay; the window is centred there
+        w = torch.sinc(x) * (0.5 + 0.5 * torch.cos(math.pi * x / (taps + 1))) * amp[:, None]
+        valid = (idx >= 0) & (idx < n_out)
+        out[m].index_add_(0, idx[valid].long(), w[valid])
+    return out.float()
+
+
 def far_field_delays(xyz: np.ndarray, direction: np.ndarray, fs: float,
                      c: float = SPEED_OF_SOUND) -> np.ndarray:
     """Per-mic delay (samples) of a far-field source from `direction`."""
