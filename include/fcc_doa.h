@@ -36,6 +36,7 @@ typedef struct fcc_doa fcc_doa_t;
  */
 fcc_status_t fcc_doa_create(fcc_plan_t *plan, const double *mic_xyz, const double *dirs, int n_dirs,
                             fcc_doa_t **out);
+/* Release a search object (NULL is ignored); safe after its plan was destroyed. */
 void fcc_doa_destroy(fcc_doa_t *doa);
 
 /*

@@ -26,6 +26,7 @@
 
 struct fcc_doa {
     fcc_plan *plan = nullptr;
+    int device = 0;         // the plan's device, kept so that destroy never reads the plan
     int D = 0, P = 0, I = 0;
     int F = 1, per_sm = 1;  // frames per search tile, resident search CTAs per SM
     int2 *d_tab = nullptr;  // [P][D] in search order: (k, bits of w), position k + w on the lag grid
@@ -316,6 +317,7 @@ fcc_status_t fcc_doa_create(fcc_plan_t *plan, const double *mic_xyz, const doubl
     fcc_doa *doa = new (std::nothrow) fcc_doa;
     if (!doa) return fail(FCC_ERR_OOM, "host allocation");
     doa->plan = plan;
+    doa->device = plan->device;
     doa->D = D;
     doa->P = P;
     doa->I = I;
@@ -342,7 +344,7 @@ fcc_status_t fcc_doa_create(fcc_plan_t *plan, const double *mic_xyz, const doubl
 void fcc_doa_destroy(fcc_doa_t *doa)
 {
     if (!doa) return;
-    DeviceScope scope(doa->plan->device);
+    DeviceScope scope(doa->device);
     cudaFree(doa->d_tab);
     cudaFree(doa->d_orig);
     delete doa;
