@@ -28,7 +28,8 @@ typedef struct fcc_doa fcc_doa_t;
 
 /*
  * plan: the FCC plan whose lag grid (L, den, I) and fs, c define the search;
- * it is borrowed and must outlive the search object.  mic_xyz: host [M][3]
+ * it is borrowed and must stay alive while the object searches (destroying
+ * the object afterwards is safe).  mic_xyz: host [M][3]
  * metres (M = the plan's microphones), copied.  dirs: host [n_dirs][3] unit
  * vectors (used as given), copied; n_dirs >= 1.  Synchronous (uploads a
  * table of P * n_dirs grid positions).
@@ -36,6 +37,7 @@ typedef struct fcc_doa fcc_doa_t;
  */
 fcc_status_t fcc_doa_create(fcc_plan_t *plan, const double *mic_xyz, const double *dirs, int n_dirs,
                             fcc_doa_t **out);
+
 /* Release a search object (NULL is ignored); safe after its plan was destroyed. */
 void fcc_doa_destroy(fcc_doa_t *doa);
 
