@@ -14,6 +14,10 @@
 //   4. one store into shared memory at index i + i / R1 (bank-conflict free for a
 //      fixed register), then the split above reads Z[k] and Z[H - k].
 //
+// For N = 512 (R1 = 8) step 3 is instead 8 x 4: one shared-memory transpose, an
+// 8-point DFT in registers, the twiddles W_32^{b c}, and a 4-point DFT over two
+// shuffle stages (fewer shuffles and twiddle products than five lane stages).
+//
 // stft_kernel<N, S>: one warp per (frame, microphone); twiddles and the window
 // are tables computed in FP64 on the host.
 #include <algorithm>
@@ -76,6 +80,11 @@ __global__ void __launch_bounds__(32 * kStftWarps) stft_kernel(const __grid_cons
         ct[s] = (lane & h) ? tw[(lane % h) * (16 / h) * (H / 32)] : make_float2(1.f, 0.f);
     }
     const int k2 = (int)(__brev((unsigned)lane) >> 27);
+    // N = 512 (R1 = 8): the 32-point DFT is 8 x 4 through a shared-memory transpose;
+    // lane (k1, b) = (lane / 4, lane % 4) keeps the twiddles W_32^{b c} for c = bitrev3(q)
+    float2 t32[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t32[q] = tw[((lane & 3) * bitrev(q, 3) * (H / 32)) & (H - 1)];
     const float scale = sizeof(S) == 2 ? 1.f / 32768.f : 1.f;
     const long long items = p.T * p.M;
     const S *pcm = static_cast<const S *>(p.pcm);
@@ -106,31 +115,77 @@ __global__ void __launch_bounds__(32 * kStftWarps) stft_kernel(const __grid_cons
         // 2. twiddle W_H^{n2 k1}
 #pragma unroll
         for (int r = 1; r < R1; ++r) v[r] = cmul(v[r], tw[lane * bitrev(r, LB)]);
-        // 3. 32-point DFT across the lanes
+        if constexpr (R1 == 8) {
+            // 3. 32-point DFT over n2 = 4 a + b (k2 = c + 8 d): row k1 of the transpose
+            //    at stride 36 (conflict-free both ways), an 8-point DFT over a in
+            //    registers, W_32^{b c}, then a 4-point DFT over b across lanes
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
-            const int h = 16 >> s;
-            const float sg = (lane & h) ? -1.f : 1.f;
+            for (int r = 0; r < 8; ++r) buf[bitrev(r, 3) * 36 + lane] = v[r];
+            __syncwarp();
+            const int k1 = lane >> 2, b = lane & 3;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) v[a] = buf[k1 * 36 + 4 * a + b];
+            __syncwarp();
+#pragma unroll
+            for (int h = 4; h >= 1; h /= 2) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q & h) continue;
+                    const float2 a = v[q], c = v[q + h];
+                    const int i = q % h;
+                    v[q] = make_float2(a.x + c.x, a.y + c.y);
+                    const float2 d = make_float2(a.x - c.x, a.y - c.y);
+                    v[q + h] = i == 0 ? d : cmul(d, tw[i * (8 / (2 * h)) * (H / 8)]);
+                }
+            }
+#pragma unroll
+            for (int q = 1; q < 8; ++q) v[q] = cmul(v[q], t32[q]);
+#pragma unroll
+            for (int h = 2; h >= 1; h /= 2) {
+                const float sg = (lane & h) ? -1.f : 1.f;
+                const bool rot = h == 2 && (lane & 2) && (lane & 1);  // W_4^1 = -i on the lower half
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float ox = __shfl_xor_sync(FULLM, v[q].x, h), oy = __shfl_xor_sync(FULLM, v[q].y, h);
+                    const float2 tv = make_float2(fmaf(sg, v[q].x, ox), fmaf(sg, v[q].y, oy));
+                    v[q] = rot ? make_float2(tv.y, -tv.x) : tv;
+                }
+            }
+            // 4. Z[k1 + 8 c + 64 d] (d = bitrev2(b)) at index i + 4 (i >> 6)
+            const int d = ((b & 1) << 1) | (b >> 1);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = k1 + 8 * bitrev(q, 3) + 64 * d;
+                buf[i + 4 * (i >> 6)] = v[q];
+            }
+        } else {
+            // 3. 32-point DFT across the lanes
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const int h = 16 >> s;
+                const float sg = (lane & h) ? -1.f : 1.f;
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const float ox = __shfl_xor_sync(FULLM, v[r].x, h), oy = __shfl_xor_sync(FULLM, v[r].y, h);
+                    float2 tv = make_float2(fmaf(sg, v[r].x, ox), fmaf(sg, v[r].y, oy));
+                    if (s < 4) tv = cmul(tv, ct[s]);
+                    v[r] = tv;
+                }
+            }
+            // 4. Z[k1 + R1 k2] into the buffer at index i + i / R1
 #pragma unroll
             for (int r = 0; r < R1; ++r) {
-                const float ox = __shfl_xor_sync(FULLM, v[r].x, h), oy = __shfl_xor_sync(FULLM, v[r].y, h);
-                float2 tv = make_float2(fmaf(sg, v[r].x, ox), fmaf(sg, v[r].y, oy));
-                if (s < 4) tv = cmul(tv, ct[s]);
-                v[r] = tv;
+                const int i = bitrev(r, LB) + R1 * k2;
+                buf[i + (i >> LB)] = v[r];
             }
-        }
-        // 4. Z[k1 + R1 k2] into the buffer at index i + i / R1
-#pragma unroll
-        for (int r = 0; r < R1; ++r) {
-            const int i = bitrev(r, LB) + R1 * k2;
-            buf[i + (i >> LB)] = v[r];
         }
         __syncwarp();
         // split into the H + 1 bins of the real frame
         float2 *out = p.out + (size_t)it * B;
         for (int k = lane; k <= H; k += 32) {
             const int i0 = k & (H - 1), i1 = (H - k) & (H - 1);
-            const float2 zk = buf[i0 + (i0 >> LB)], zm = buf[i1 + (i1 >> LB)];
+            const float2 zk = R1 == 8 ? buf[i0 + 4 * (i0 >> 6)] : buf[i0 + (i0 >> LB)];
+            const float2 zm = R1 == 8 ? buf[i1 + 4 * (i1 >> 6)] : buf[i1 + (i1 >> LB)];
             const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
             const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));  // (Z[k] - Z*[H-k]) / 2i
             const float2 w = cmul(sp[k], O);
