@@ -291,6 +291,22 @@ def run_fcc(args, rank, world, local):
     plan.sync()
     gms = g0.elapsed_time(g1) / gsteps
     agree = float((gout["lag_idx"] == out["lag_idx"]).float().mean().item())
+    # the paper's GCC setting, r = 2 (a grid of step 1/2 over the same lag range), for context
+    gcc2 = None
+    if w.lag_den != 2:
+        p2 = binding.Plan(w.M, w.fs, w.N, 2, tau_max=w.L, device=local)
+        g2 = p2.gcc_tdoa(X)
+        torch.cuda.synchronize(dev)
+        g0.record(stream)
+        for _ in range(gsteps):
+            p2.gcc_tdoa(X, out=g2)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        p2.sync()
+        g2ms = g0.elapsed_time(g1) / gsteps
+        gcc2 = {"value": world * T * P / (g2ms / 1000.0), "unit": UNIT, "ms_per_step": g2ms, "r": 2}
+        del g2
+        p2.close()
 
     # ---- end to end through the host entry point (pinned host in, host out)
     Xh = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
@@ -346,6 +362,7 @@ def run_fcc(args, rank, world, local):
             "roofline_alu": alu_roofline(ops_pf * T * P, ms, "fcc_fp32_kernel") if args.prec == "fp32" else None,
             "gcc_phat": {"value": world * T * P / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms,
                          "r": w.lag_den, "argmax_agreement_with_fcc": agree},
+            "gcc_phat_r2": gcc2,
             "fcc_vs_gcc": (gms / ms),
             "flops_per_pair_frame": {"fcc_paper": flops.fcc_flops(w.N, plan.I, plan.K),
                                      "gcc_paper_r": flops.gcc_flops(w.N, w.lag_den)},
