@@ -49,6 +49,7 @@ struct SmoothParams {
     float *out_coef;
     unsigned *err;
     long long wait_cycles;
+    int inject;             // test hook: CTA 0 withholds the copy of its first frame
 };
 
 // Pass 1: the recursion run from zero over each chunk.  One CTA per chunk, one
@@ -240,8 +241,12 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                  (unsigned)frame_bytes, &full[s]);
     };
     long long issued = 0, g = 0;
+    // the test hook withholds CTA 0's first frame: every warp's first wait runs out
+    // (bounded), the launch finishes and the error word reports the timeout
+    const long long withheld = (p.inject && blockIdx.x == 0) ? 0 : -1;
     if (threadIdx.x == 0)
-        for (; issued < kSmoothStages && issued < total_g; ++issued) issue(issued);
+        for (; issued < kSmoothStages && issued < total_g; ++issued)
+            if (issued != withheld) issue(issued);
     const f2 beta2 = pk(p.beta, p.beta);
     for (int ci = 0; ci < my_chunks && !failed; ++ci) {
         const int c = (int)blockIdx.x + ci * (int)gridDim.x;
@@ -465,9 +470,11 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
     if (__any_sync(FULLM, bad) && lane == 0) atomicOr(p.err, kErrNonFinite);
     if (failed && threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
     // never retire with a bulk copy in flight: frames issued but not consumed
+    // (a withheld frame was never issued, so there is nothing to wait for)
     if (threadIdx.x == 0)
         for (long long h = g; h < issued; ++h)
-            if (!mbar_wait(&full[h % kSmoothStages], (unsigned)(h / kSmoothStages) & 1u, p.wait_cycles)) {
+            if (h != withheld &&
+                !mbar_wait(&full[h % kSmoothStages], (unsigned)(h / kSmoothStages) & 1u, p.wait_cycles)) {
                 atomicOr(p.err, kErrTimeout);
                 break;
             }
@@ -602,7 +609,13 @@ fcc_status_t run_per_pair(const fcc_plan *plan, const SmoothPlan &g, const float
     prm.out_tau = tau;
     prm.out_coef = coef;
     prm.err = plan->d_err;
-    prm.wait_cycles = debug_hooks().wait_cycles;
+    DebugHooks &dh = debug_hooks();
+    prm.wait_cycles = dh.wait_cycles;
+    prm.inject = 0;
+    if (dh.withhold_copies > 0) {
+        --dh.withhold_copies;
+        prm.inject = 1;
+    }
     const int rs = in.Q / 32;
     return is_split(plan) ? launch_smooth_form<true>(plan->kh, rs, prm, plan->num_sms, g.threads, g.smem, s)
                           : launch_smooth_form<false>(plan->kh, rs, prm, plan->num_sms, g.threads, g.smem, s);

@@ -86,3 +86,29 @@ def test_allocation_failure_during_plan_creation(hooks):
     assert e.value.status == OOM
     plan = B.Plan(4, 16000.0, 512, 4, tau_max=3)  # the hook is spent
     plan.close()
+
+
+@pytest.mark.parametrize("form,alpha", [("folded", 0.1), ("reim", 1.0)])
+def test_per_pair_kernel_timeout_path(hooks, form, alpha):
+    # the per-pair kernel (smoothed path; split form) takes the same exit: its
+    # first frame withheld in CTA 0, a short wait bound, FCC_ERR_TIMEOUT, and the
+    # next launch on the same context equal to the reference
+    B = hooks
+    plan = B.Plan(8, 16000.0, 512, 4, tau_max=5, form=form)
+    X = _spectra(3000, 8, 2)
+    run = (lambda: plan.tdoa_smoothed(X, alpha)) if alpha < 1.0 else (lambda: plan.tdoa(X))
+    ref = run()
+    plan.sync()
+    ref = {k: v.clone() for k, v in ref.items()}
+    B.debug_set("wait_cycles", 200000)  # about 0.1 ms
+    B.debug_set("withhold_copy", 1)
+    run()
+    with pytest.raises(B.FccError) as e:
+        plan.sync()
+    assert e.value.status == TIMEOUT
+    B.debug_set("wait_cycles", 0)
+    out = run()
+    plan.sync()
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
+    plan.close()
