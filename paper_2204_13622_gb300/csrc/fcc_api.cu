@@ -344,6 +344,12 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
         free_plan(p);
         return cuda_fail(e, "plan tables");
     }
+    if (in.form == FCC_FORM_FOLDED && in.prec == FCC_PREC_FP32 && p->kh) st = prepare_per_pair(p);
+    if (st == FCC_OK) st = prepare_stft(p);
+    if (st != FCC_OK) {
+        free_plan(p);
+        return st;
+    }
     if (in.prec != FCC_PREC_FP32) {
         st = prepare_tc(p);
         if (st != FCC_OK) {

@@ -224,6 +224,9 @@ inline fcc_status_t launch_tdoa(const fcc_plan *plan, const float2 *spectra, lon
                                             : launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
 }
 void pcm_destroy(fcc_plan *plan);
+// Plan-time tables of the per-pair kernel (folded form) and of the STFT front-end.
+fcc_status_t prepare_per_pair(fcc_plan *plan);
+fcc_status_t prepare_stft(fcc_plan *plan);
 fcc_status_t gcc_run(fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                      float *corr, cudaStream_t st);
 void gcc_destroy(fcc_plan *plan);

@@ -553,9 +553,12 @@ fcc_status_t launch_smooth_form(int kh, int rs, const SmoothParams &prm, int num
     }
 }
 
+}  // namespace
+
 // Folded-form weights in the per-pair kernel's layout: row v < KH = even basis v
 // over records 0..Q, row KH + v = odd basis v (zero at Q); padding records zero.
-fcc_status_t folded_weights(fcc_plan *plan)
+// Built when the plan is created, so the smoothed path never allocates.
+fcc_status_t prepare_per_pair(fcc_plan *plan)
 {
     if (plan->d_smooth_basis) return FCC_OK;
     const fcc_plan_info_t &in = plan->info;
@@ -576,6 +579,8 @@ fcc_status_t folded_weights(fcc_plan *plan)
     plan->d_smooth_basis = d;
     return FCC_OK;
 }
+
+namespace {
 
 // The per-pair kernel over T frames: `carry` (may be null: every chunk starts
 // from R = 0, which is exact for alpha = 1) holds the state entering each chunk.
@@ -739,10 +744,7 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "smoothing carry kernels");
     }
-    if (!is_split(plan)) {
-        st = folded_weights(plan);
-        if (st != FCC_OK) return st;
-    }
+    if (!plan->d_smooth_basis) return fail(FCC_ERR_UNSUPPORTED, "the plan has no per-pair tables");
     return run_per_pair(plan, g, static_cast<const float2 *>(d_spectra), T, a, b, work, d_lag_idx, d_peak, d_tau_hat,
                         d_coeffs, s);
 }

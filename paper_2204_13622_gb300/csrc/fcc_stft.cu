@@ -201,9 +201,12 @@ size_t stft_smem(int N)
     return (size_t)(H + H + 2) * sizeof(float2) + (size_t)N * sizeof(float) + (size_t)kStftWarps * (H + 32) * sizeof(float2);
 }
 
-fcc_status_t stft_tables(fcc_plan *plan)
+}  // namespace
+
+// Twiddles and window of the STFT front-end, built when the plan is created (64 <= N <= 2048).
+fcc_status_t prepare_stft(fcc_plan *plan)
 {
-    if (plan->d_stft_tab) return FCC_OK;
+    if (plan->d_stft_tab || plan->info.N < 64 || plan->info.N > 2048) return FCC_OK;
     const int N = plan->info.N, H = N / 2;
     std::vector<float> tab((size_t)2 * H + 2 * (H + 1) + N);
     const double two_pi = 6.283185307179586476925286766559;
@@ -226,6 +229,8 @@ fcc_status_t stft_tables(fcc_plan *plan)
     plan->d_stft_tab = d;
     return FCC_OK;
 }
+
+namespace {
 
 template <int N, typename S>
 fcc_status_t launch_stft_n(const StftParams &prm, int num_sms, cudaStream_t st)
@@ -251,8 +256,7 @@ fcc_status_t launch_stft_t(const StftParams &prm, int num_sms, cudaStream_t st)
 
 fcc_status_t launch_stft(fcc_plan *plan, const void *pcm, int type, long long T, int hop, float2 *out, cudaStream_t st)
 {
-    fcc_status_t s = stft_tables(plan);
-    if (s != FCC_OK) return s;
+    if (!plan->d_stft_tab) return fail(FCC_ERR_UNSUPPORTED, "the STFT front-end needs 64 <= N <= 2048");
     StftParams prm{};
     prm.pcm = pcm;
     prm.type = type;
