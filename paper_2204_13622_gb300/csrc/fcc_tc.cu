@@ -19,9 +19,11 @@
 //     tiles are full (FP32 accumulators, two TMEM buffers so that a tile's
 //     epilogue overlaps the next tile's MMAs) and commits them to mbarriers;
 //   * 1 copy warp: streams raw frame tiles with one cp.async.bulk per tile.
-// Epilogue (producer warps 0..3, warp q owns pair q of every slot): tcgen05.ld
-// of the pair's 2K coefficients, the lone bin N/4 added in FP32, then the same
-// FP32 lag-grid reconstruction, argmax and refinement as the FP32 path.
+// Epilogue (8 warps of their own, two per TMEM lane quadrant = pair q of every
+// slot, a tile behind the producers): tcgen05.ld of the pair's 2K
+// coefficients, the lone bin N/4 (from the producers, through shared memory)
+// added in FP32, then the FP32 lag-grid reconstruction split between the two
+// warps of the quadrant, argmax and refinement as the FP32 path.
 // Every wait is bounded; TMEM is released on every exit path.
 #include <algorithm>
 #include <cfloat>
@@ -36,7 +38,9 @@ namespace fcc {
 namespace {
 
 constexpr int kProdWarps = 8;                 // producer warps (one 4-bin group each)
-constexpr int kThreadsTC = (kProdWarps + 2) * 32;
+constexpr int kEpiWarps = 8;                 // epilogue warps: two per TMEM lane quadrant (pair q)
+constexpr int kEpi0 = kProdWarps + 2;         // first epilogue warp
+constexpr int kThreadsTC = (kProdWarps + 2 + kEpiWarps) * 32;
 constexpr int kChunkRec = 4 * kProdWarps;     // bins per chunk (32)
 constexpr int kChunkCols = 2 * kChunkRec;     // A columns per part per chunk (64)
 constexpr int kPartBytes = 128 * kChunkCols * 2;  // one part of one chunk (16 KB)
@@ -44,7 +48,7 @@ constexpr int kNTile = 16;                    // MMA N: (c', n) with n < 8
 constexpr int kTmemCols = 64;                 // two (even, odd) accumulator buffers
 
 struct TcLayout {
-    size_t bar, slot, bas_e, bas_o, peq, recon, abuf, ubuf, raw, total;
+    size_t bar, slot, bas_e, bas_o, peq, recon, lone, comb, abuf, ubuf, raw, total;
     int ustride;  // bytes per unit-phase row
 };
 
@@ -54,7 +58,7 @@ __host__ __device__ inline TcLayout tc_layout(int n_slots, int Q, int kh, int ce
     TcLayout L;
     size_t o = 0;
     L.bar = o;
-    o += 16 * 8 + 16;  // mbarriers + TMEM address
+    o += 32 * 8 + 16;  // mbarriers + TMEM address
     o = (o + 15) & ~(size_t)15;
     L.slot = o;
     o += (size_t)n_slots * sizeof(Slot);
@@ -68,6 +72,11 @@ __host__ __device__ inline TcLayout tc_layout(int n_slots, int Q, int kh, int ce
     o = (o + 15) & ~(size_t)15;
     L.recon = o;
     o += (size_t)(center + 1) * 4 * kh * sizeof(float);
+    o = (o + 15) & ~(size_t)15;
+    L.lone = o;  // [2][4][32] float2: the lone bin's cross spectrum per tile parity, pair, slot
+    o += 2 * 4 * 32 * 8;
+    L.comb = o;  // [2][4][32] (float, int): the second half's maximum per tile parity, pair, slot
+    o += 2 * 4 * 32 * 8;
     o = (o + 127) & ~(size_t)127;
     L.abuf = o;
     o += 2 * 2 * (size_t)kPartBytes;
@@ -114,6 +123,14 @@ enum {
     kDFull1,
     kDEmpty0,      // accumulator buffer 0 / 1 read by the epilogue
     kDEmpty1,
+    kLoneFull0,    // the lone bin of tile parity 0 / 1 written by producers 0..3
+    kLoneFull1,
+    kLoneFree0,    // ... read by the epilogue warps
+    kLoneFree1,
+    kCombFull0,    // the second half's maxima of tile parity 0 / 1 written
+    kCombFull1,
+    kCombFree0,    // ... read by the first half
+    kCombFree1,
     kNumBars
 };
 
@@ -129,6 +146,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
     Slot *slots = reinterpret_cast<Slot *>(smem + lay.slot);
     float *peq = reinterpret_cast<float *>(smem + lay.peq);
     float *recon = reinterpret_cast<float *>(smem + lay.recon);
+    float2 *lone_buf = reinterpret_cast<float2 *>(smem + lay.lone);
+    float *comb_s = reinterpret_cast<float *>(smem + lay.comb);
+    int *comb_i = reinterpret_cast<int *>(smem + lay.comb) + 2 * 4 * 32;
     unsigned char *abuf = smem + lay.abuf;
     unsigned char *ubuf = smem + lay.ubuf;
     unsigned char *raw = smem + lay.raw;
@@ -151,8 +171,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
         mbar_init(&bar[kAEmpty1], 1);
         mbar_init(&bar[kDFull0], 1);
         mbar_init(&bar[kDFull1], 1);
-        mbar_init(&bar[kDEmpty0], 4);
-        mbar_init(&bar[kDEmpty1], 4);
+        mbar_init(&bar[kDEmpty0], kEpiWarps);
+        mbar_init(&bar[kDEmpty1], kEpiWarps);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[kLoneFull0 + b], 4);
+            mbar_init(&bar[kLoneFree0 + b], kEpiWarps);
+            mbar_init(&bar[kCombFull0 + b], kEpiWarps / 2);
+            mbar_init(&bar[kCombFree0 + b], kEpiWarps / 2);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
@@ -247,7 +273,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
                 if (!mbar_wait(&bar[kAEmpty0 + b], (unsigned)((cc - 1) >> 1) & 1u)) atomicOr(p.err, kErrTimeout);
             }
         }
-    } else {
+    } else if (warp < kProdWarps) {
         // ================= producer warps =================
         const int g = warp;         // bin group within a chunk
         const int sp = lane;        // slot within the tile
@@ -314,20 +340,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
             const uint2 *u1 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[1]) * lay.ustride);
             const uint2 *u2 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[2]) * lay.ustride);
             const uint2 *u3 = reinterpret_cast<const uint2 *>(ubuf + (size_t)(R0 + sl.mic[3]) * lay.ustride);
-            // the lone bin N/4 of this thread's own pair (q = warp for warps 0..3)
-            float lone_r = 0.f, lone_i = 0.f;
-            if (warp < 4 && live) {
-                const int q = warp;
-                const __half2 hx = *reinterpret_cast<const __half2 *>(
-                    ubuf + (size_t)(R0 + sl.mic[q >> 1]) * lay.ustride + 8 * Q);
-                const __half2 hy = *reinterpret_cast<const __half2 *>(
-                    ubuf + (size_t)(R0 + sl.mic[2 + (q & 1)]) * lay.ustride + 8 * Q);
-                const float2 x = __half22float2(hx), y = __half22float2(hy);
-                lone_r = fmaf(x.x, y.x, x.y * y.y);
-                lone_i = fmaf(x.y, y.x, -(x.x * y.y));
-            }
+            // the lone bin N/4 of this thread's own pair (q = warp for warps 0..3), for
+            // the epilogue warps: its buffer (tile parity) is free once they read it
+            // two tiles ago
             bool ok = true;
-            for (int ch = 0; ch < nch; ++ch, ++cc) {
+            if (warp < 4) {
+                const int db = k & 1;
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar[kLoneFree0 + db], ((unsigned)(k >> 1) & 1u) ^ 1u))) {
+                    ok = false;
+                } else {
+                    float lone_r = 0.f, lone_i = 0.f;
+                    if (live) {
+                        const int q = warp;
+                        const __half2 hx = *reinterpret_cast<const __half2 *>(
+                            ubuf + (size_t)(R0 + sl.mic[q >> 1]) * lay.ustride + 8 * Q);
+                        const __half2 hy = *reinterpret_cast<const __half2 *>(
+                            ubuf + (size_t)(R0 + sl.mic[2 + (q & 1)]) * lay.ustride + 8 * Q);
+                        const float2 x = __half22float2(hx), y = __half22float2(hy);
+                        lone_r = fmaf(x.x, y.x, x.y * y.y);
+                        lone_i = fmaf(x.y, y.x, -(x.x * y.y));
+                    }
+                    lone_buf[(db * 4 + warp) * 32 + sp] = make_float2(lone_r, lone_i);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar[kLoneFull0 + db]);
+                }
+            }
+            for (int ch = 0; ch < nch && ok; ++ch, ++cc) {
                 const int b = (int)(cc & 1);
                 if (!mbar_wait(&bar[kAEmpty0 + b], ((unsigned)(cc >> 1) & 1u) ^ 1u)) {
                     ok = false;
@@ -368,87 +406,148 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fcc_tc_kernel(const TcParams p)
                 if (lane == 0) atomicOr(p.err, kErrTimeout);
                 break;
             }
-            // ---- epilogue: warps 0..3, thread = pair q = warp of slot sp
-            if (warp < 4) {
-                const int db = k & 1;
-                if (!mbar_wait(&bar[kDFull0 + db], (unsigned)(k >> 1) & 1u)) {
-                    if (lane == 0) atomicOr(p.err, kErrTimeout);
+        }
+    } else {
+        // ================= epilogue warps =================
+        // Warp w reads TMEM lane quadrant w % 4, i.e. pair q of every slot; the two
+        // warps of a quadrant split the lag steps (half h = 0: m < mid, including
+        // m = 0; h = 1: the rest) and h = 0 takes the larger of the two maxima
+        // (lowest index on a tie) and writes the outputs (every wait's outcome is
+        // made warp-uniform before the warp acts on it).  They run a tile behind
+        // the producers (two accumulator buffers), so reconstruction overlaps
+        // the next tile's PHAT and A tiles.
+        const int q = warp & 3, h = (warp - kEpi0) >> 2;
+        const int sp = lane;
+        const int TS = p.F * p.n_slots;
+        const bool live = sp < TS;
+        const int fl = live ? sp / p.n_slots : 0;
+        Slot sl{};
+        if (live) sl = slots[sp - fl * p.n_slots];
+        const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
+        const int mid = (p.center + 1) / 2;
+        bool ok = true;
+        for (int k = 0; k < n_local; ++k) {
+            int nf;
+            const long long f0 = tile_src(k, nf);
+            const int db = k & 1;
+            const unsigned par = (unsigned)(k >> 1) & 1u;
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[kDFull0 + db], par))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float de[16], dd[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + db * 32;
+            tmem_ld16(taddr, de);
+            tmem_ld16(taddr + 16, dd);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[kDEmpty0 + db]);
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[kLoneFull0 + db], par))) {
+                ok = false;
+                break;
+            }
+            const float2 lone = lone_buf[(db * 4 + q) * 32 + sp];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[kLoneFree0 + db]);
+            const bool act = live && fl < nf && pq >= 0;
+            f2 zE[KH], zO[KH];
+#pragma unroll
+            for (int v = 0; v < KH; ++v) {
+                zE[v] = pk(fmaf(peq[v], lone.x, de[v]), fmaf(peq[v], lone.y, de[8 + v]));
+                zO[v] = pk(dd[v], dd[8 + v]);
+            }
+            const size_t o = act ? (size_t)(f0 + fl) * p.P + pq : 0;
+            float *corr = (act && p.out_corr) ? p.out_corr + o * p.I : nullptr;
+            float best = -FLT_MAX;
+            int bi = 0x7fffffff;
+            if (act) {
+                float S, D;
+                int m = mid;
+                if (h == 0) {
+                    eval_SD<KH>(recon, 0, zE, zO, S, D);
+                    best = S - D;
+                    bi = p.center;
+                    if (corr) corr[p.center] = best;
+                    m = 1;
+                }
+                const int m_end = h == 0 ? mid : p.center + 1;
+                for (; m < m_end; ++m) {
+                    eval_SD<KH>(recon, m, zE, zO, S, D);
+                    const float ym = S + D, yp = S - D;
+                    if (ym >= best) {
+                        best = ym;
+                        bi = p.center - m;
+                    }
+                    if (yp > best) {
+                        best = yp;
+                        bi = p.center + m;
+                    }
+                    if (corr) {
+                        corr[p.center - m] = ym;
+                        corr[p.center + m] = yp;
+                    }
+                }
+            }
+            const int ci = (db * 4 + q) * 32 + sp;
+            if (h == 1) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar[kCombFree0 + db], par ^ 1u))) {
+                    ok = false;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float de[16], dd[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + db * 32;
-                tmem_ld16(taddr, de);
-                tmem_ld16(taddr + 16, dd);
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                comb_s[ci] = best;
+                comb_i[ci] = bi;
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar[kDEmpty0 + db]);
-                const int q = warp;
-                const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
-                if (live && fl < nf && pq >= 0) {
-                    f2 zE[KH], zO[KH];
+                if (lane == 0) mbar_arrive(&bar[kCombFull0 + db]);
+                continue;
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[kCombFull0 + db], par))) {
+                ok = false;
+                break;
+            }
+            const float ob = comb_s[ci];
+            const int oi = comb_i[ci];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[kCombFree0 + db]);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+            if (act) {
+                p.out_idx[o] = bi;
+                p.out_peak[o] = best;
+                if (p.out_tau) {
+                    float off = 0.f;
+                    if (bi > 0 && bi < p.I - 1) {
+                        const double y_m = y_at<KH>(recon, p.center, bi - 1, zE, zO);
+                        const double y_p = y_at<KH>(recon, p.center, bi + 1, zE, zO);
+                        const double num = y_m - y_p;
+                        const double den = (y_m - 2.0 * (double)best) + y_p;
+                        if (den < 0.0) off = fminf(0.5f, fmaxf(-0.5f, 0.5f * (float)num / (float)den));
+                    }
+                    p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
+                }
+                if (p.out_coef) {
+                    const int K = p.KE + p.KO;
+                    float *cf = p.out_coef + o * 2 * K;
 #pragma unroll
                     for (int v = 0; v < KH; ++v) {
-                        zE[v] = pk(fmaf(peq[v], lone_r, de[v]), fmaf(peq[v], lone_i, de[8 + v]));
-                        zO[v] = pk(dd[v], dd[8 + v]);
-                    }
-                    const size_t o = (size_t)(f0 + fl) * p.P + pq;
-                    float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
-                    float S, D;
-                    eval_SD<KH>(recon, 0, zE, zO, S, D);
-                    float best = S - D;
-                    int bi = p.center;
-                    if (corr) corr[p.center] = best;
-                    for (int m = 1; m <= p.center; ++m) {
-                        eval_SD<KH>(recon, m, zE, zO, S, D);
-                        const float ym = S + D, yp = S - D;
-                        if (ym >= best) {
-                            best = ym;
-                            bi = p.center - m;
+                        float a, b2;
+                        if (v < p.KE) {
+                            upk(zE[v], a, b2);
+                            cf[v] = a;
+                            cf[p.KE + v] = b2;
                         }
-                        if (yp > best) {
-                            best = yp;
-                            bi = p.center + m;
-                        }
-                        if (corr) {
-                            corr[p.center - m] = ym;
-                            corr[p.center + m] = yp;
-                        }
-                    }
-                    p.out_idx[o] = bi;
-                    p.out_peak[o] = best;
-                    if (p.out_tau) {
-                        float off = 0.f;
-                        if (bi > 0 && bi < p.I - 1) {
-                            const double y_m = y_at<KH>(recon, p.center, bi - 1, zE, zO);
-                            const double y_p = y_at<KH>(recon, p.center, bi + 1, zE, zO);
-                            const double num = y_m - y_p;
-                            const double den = (y_m - 2.0 * (double)best) + y_p;
-                            if (den < 0.0) off = fminf(0.5f, fmaxf(-0.5f, 0.5f * (float)num / (float)den));
-                        }
-                        p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
-                    }
-                    if (p.out_coef) {
-                        const int K = p.KE + p.KO;
-                        float *cf = p.out_coef + o * 2 * K;
-#pragma unroll
-                        for (int v = 0; v < KH; ++v) {
-                            float a, b2;
-                            if (v < p.KE) {
-                                upk(zE[v], a, b2);
-                                cf[v] = a;
-                                cf[p.KE + v] = b2;
-                            }
-                            if (v < p.KO) {
-                                upk(zO[v], a, b2);
-                                cf[2 * p.KE + v] = a;
-                                cf[2 * p.KE + p.KO + v] = b2;
-                            }
+                        if (v < p.KO) {
+                            upk(zO[v], a, b2);
+                            cf[2 * p.KE + v] = a;
+                            cf[2 * p.KE + p.KO + v] = b2;
                         }
                     }
                 }
             }
         }
+        if (!ok && lane == 0) atomicOr(p.err, kErrTimeout);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
