@@ -415,14 +415,28 @@ FP32_PEAK_OPS = 152 * 128 * 2.070e9
 def fp32_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float:
     """FP32 operations per pair-frame of the FP32 kernel's arithmetic (FMA = 1):
     the cross spectrum (4 per bin), the Eq. 8 fold (4 per bin pair), the even and
-    odd projections (2 per basis and bin), the reconstruction over tau >= 0 (4K + 2
-    per lag step, both signs at once) and this pair's share of the per-microphone
-    PHAT (5 per microphone bin)."""
+    odd projections (2 per basis and bin), the reconstruction over tau >= 0 (per
+    lag step m, S = sum of K weights times Re z and D = sum of K weights times
+    Im z, then y(-m) = S + D and y(+m) = S - D: 2K + 2) and this pair's share of
+    the per-microphone PHAT (5 per microphone bin)."""
     B, Q = N // 2 + 1, N // 4
     P = M * (M - 1) // 2
     center = (I - 1) // 2
-    return (4 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (4 * (KE + KO) + 2)
+    return (4 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (2 * (KE + KO) + 2)
             + 5.0 * M * B / P)
+
+
+def reim_ops_per_pair_frame(M: int, N: int, Kc: int, Ks: int, I: int) -> float:
+    """FP32 operations per pair-frame of the split form at alpha = 1 (FMA = 1):
+    the cross spectrum (4 per bin), the cosine and sine projections (one per
+    basis and bin: c = C_K-rows . Re x, s = S_K-rows . Im x, no fold), the
+    reconstruction over tau >= 0 (K_c + K_s + 2 per lag step, both signs at
+    once) and this pair's share of the per-microphone PHAT (5 per microphone
+    bin)."""
+    B = N // 2 + 1
+    P = M * (M - 1) // 2
+    center = (I - 1) // 2
+    return 4 * B + (Kc + Ks) * B + (center + 1) * (Kc + Ks + 2) + 5.0 * M * B / P
 
 
 def smooth_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float:
@@ -434,7 +448,7 @@ def smooth_ops_per_pair_frame(M: int, N: int, KE: int, KO: int, I: int) -> float
     counted."""
     B, Q = N // 2 + 1, N // 4
     center = (I - 1) // 2
-    return (6 * B + 12 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (4 * (KE + KO) + 2))
+    return (6 * B + 12 * B + 4 * Q + 2 * (KE * (Q + 1) + KO * Q) + (center + 1) * (2 * (KE + KO) + 2))
 
 
 SMEM_PEAK_BPS = 152 * 128 * 2.070e9  # shared memory: 128 bytes per clock per SM
@@ -752,7 +766,8 @@ def doa_chunk(doa, T):
 
 def run_split_form(args, rank, world, local):
     """The split form (cosine bases on Re x, sine bases on Im x) on the 8-mic
-    circle: fcc_tdoa on a FCC_FORM_REIM_SPLIT plan, per-pair kernel, alpha = 1."""
+    circle: fcc_tdoa on a FCC_FORM_REIM_SPLIT plan (the FP32 tile kernel's
+    split-form instance), alpha = 1."""
     import numpy as np
     import torch
 
@@ -792,10 +807,7 @@ def run_split_form(args, rank, world, local):
         idx, _, _, _ = O.tdoa(X[:n].cpu().numpy(), ob.WK, ob.taus, ob.delta)
         t_or = time.perf_counter() - t1
         got = out["lag_idx"][:n].cpu().numpy()
-        B, K, center = w.N // 2 + 1, plan.K, (plan.I - 1) // 2
-        # per bin: cross spectrum 4, recursion update 2, phase transform 6; projection
-        # 2 per (coefficient, bin); reconstruction 2 K + 2 per lag step (FMA = 1)
-        ops = T * P * (12 * B + 2 * K * B + (center + 1) * (2 * K + 2))
+        ops = T * P * reim_ops_per_pair_frame(w.M, w.N, plan.K_even, plan.K_odd, plan.I)
         bytes_alg = T * (w.M * w.B * 8) + T * P * 12
         peak, psrc = _peak_hbm()
         res = {"metric": METRIC, "value": whole_job_rate(T * P, world, ms_max / 1000.0), "unit": UNIT,
@@ -804,7 +816,7 @@ def run_split_form(args, rank, world, local):
                "data": "synthetic",
                "config": {"workload": f"{w.name}, split form (cosine / sine bases)", "frames": T, "pairs": P,
                           "K_c": plan.K_even, "K_s": plan.K_odd, "l2": "inputs larger than L2; no flush"},
-               "roofline": dict(alu_roofline(ops, ms, "fcc_smooth_kernel (split form, alpha = 1)"), traffic=None,
+               "roofline": dict(alu_roofline(ops, ms, "fcc_fp32_reim_kernel"), traffic=None,
                                 hbm={"achieved": bytes_alg / (ms / 1000.0) / 1e9, "peak": peak,
                                      "frac": bytes_alg / (ms / 1000.0) / 1e9 / peak, "peak_source": psrc}),
                "accuracy_vs_oracle": {"pair_frames": int(got.size), "argmax_agreement": float((got == idx).mean())},

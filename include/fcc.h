@@ -78,12 +78,14 @@ typedef enum {
  *   prec     an fcc_prec_t.
  *   device   CUDA device ordinal; < 0 uses the calling thread's current device.
  *   form     an fcc_form_t (0, the default, is the paper's folded form).  The
- *            split form is FP32 only and runs on the per-pair kernel of
- *            fcc_smooth.h (an even number of mics up to 8, 128 <= N <= 512); its
- *            info reports K_even = K_c (cosine bases) and K_odd = K_s (sine
- *            bases), each chosen by the energy rule on its own matrix (or both
- *            = K when K > 0), and fcc_tdoa gives no coefficient or correlation
- *            output for it.
+ *            split form is FP32 only (max(K_c, K_s) <= 16): fcc_tdoa runs it on
+ *            the FP32 tile kernel (N <= 1024, with the correlation output but
+ *            no coefficient output), fcc_tdoa_smoothed on the per-pair kernel
+ *            of fcc_smooth.h (an even number of mics up to 8,
+ *            128 <= N <= 512); the autotuner and the batched form take folded
+ *            plans only.  Its info reports K_even = K_c (cosine bases) and
+ *            K_odd = K_s (sine bases), each chosen by the energy rule on its
+ *            own matrix (or both = K when K > 0).
  */
 typedef struct {
     int n_mics;
@@ -166,7 +168,8 @@ fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, doub
  *   d_peak     device float [T][P]: y at the argmax (required).
  *   d_tau_hat  device float [T][P]: refined TDoA in samples, or NULL.
  *   d_coeffs   device float [T][P][2K]: projection coefficients in the order
- *              Re z_e (K_even), Im z_e (K_even), Re z_o (K_odd), Im z_o (K_odd); or NULL.
+ *              Re z_e (K_even), Im z_e (K_even), Re z_o (K_odd), Im z_o (K_odd); or NULL
+ *              (must be NULL for the split form: UNSUPPORTED).
  *   d_corr     device float [T][P][I]: the correlation y on the grid; or NULL.
  *   stream     cudaStream_t or NULL.
  * Asynchronous; allocates nothing.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.

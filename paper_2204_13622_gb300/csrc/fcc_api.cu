@@ -95,12 +95,47 @@ std::vector<Slot> make_slots(int M)
 //     a = cos(pi tau / 2), b = sin(pi tau / 2); then y(+tau) = S - D and
 //     y(-tau) = S + D where S = gSe.Re z_e + gSo.Re z_o and D = gDe.Im z_e + gDo.Im z_o
 //     (Ue is even and Uo odd in tau).
+// Split form (FCC_FORM_REIM_SPLIT), same row order: per coefficient v < 2 kh the
+// float4 (C_v(f), S_v(f), C_v(N/2 - f), S_v(N/2 - f)) of the cosine / sine
+// projections (sigma v of C = Re W and of S = Im W, zero past K_c / K_s), and
+// (C_v(N/4), S_v(N/4), 0, 0) in the bin N/4 row; recon row m holds per k
+// (2 U_c[k], 2 U_s[k], 2 U_c[kh + k], 2 U_s[kh + k]) at tau = m / den, so that
+// S = 2 U_c . c, D = 2 U_s . s and y(+/-tau) = S -/+ D (U_c even, U_s odd in tau).
 void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<float> &recon)
 {
     const fcc_plan_info_t &in = plan->info;
     const int kh = plan->kh, Q = in.Q, KE = in.K_even, KO = in.K_odd;
     const int C = plan->geo.C, BS = plan->geo.BS, QC = Q / C;
     basis.assign((size_t)(Q + C + 1) * BS, 0.f);
+    if (in.form == FCC_FORM_REIM_SPLIT) {
+        const int B = in.B;
+        auto cw = [&](int v, int f) { return v < KE ? (float)plan->Pe[(size_t)v * B + f] : 0.f; };
+        auto sw = [&](int v, int f) { return v < KO ? (float)plan->Po[(size_t)v * B + f] : 0.f; };
+        for (int f = 0; f <= Q; ++f) {
+            const int row = f < Q ? (f / QC) * (QC + 1) + f % QC : C * (QC + 1);
+            float *r = &basis[(size_t)row * BS];
+            for (int v = 0; v < 2 * kh; ++v) {
+                r[4 * v] = cw(v, f);
+                r[4 * v + 1] = sw(v, f);
+                if (f < Q) {
+                    r[4 * v + 2] = cw(v, 2 * Q - f);
+                    r[4 * v + 3] = sw(v, 2 * Q - f);
+                }
+            }
+        }
+        recon.assign((size_t)(in.center + 1) * 4 * kh, 0.f);
+        auto uc = [&](int i, int k) { return k < KE ? plan->Ue[(size_t)i * KE + k] : 0.0; };
+        auto us = [&](int i, int k) { return k < KO ? plan->Uo[(size_t)i * KO + k] : 0.0; };
+        for (int m = 0; m <= in.center; ++m)
+            for (int k = 0; k < kh; ++k) {
+                float *g = &recon[((size_t)m * kh + k) * 4];
+                g[0] = (float)(2.0 * uc(in.center + m, k));
+                g[1] = (float)(2.0 * us(in.center + m, k));
+                g[2] = (float)(2.0 * uc(in.center + m, kh + k));
+                g[3] = (float)(2.0 * us(in.center + m, kh + k));
+            }
+        return;
+    }
     for (int f = 0; f <= Q; ++f) {
         const int row = f < Q ? (f / QC) * (QC + 1) + f % QC : C * (QC + 1);
         float *r = &basis[(size_t)row * BS];
@@ -321,16 +356,18 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
     }
     std::vector<Slot> slots = make_slots(in.M);
     p->n_slots = (int)slots.size();
-    if (in.form == FCC_FORM_REIM_SPLIT) {
-        st = set_fp32_geometry(p, Fp32Geometry{});  // placeholder tables: the folded kernel is not used
-        if (st == FCC_OK && p->kh) st = prepare_reim(p);
+    if (p->kh) {
+        // the FP32 kernel's tables (folded or split form); the split form also
+        // gets the per-pair kernel's weights (Eq. 1 smoothing)
+        st = choose_fp32_geometry(p);
+        if (st == FCC_OK) st = set_fp32_geometry(p, p->geo);
+        if (st == FCC_OK && in.form == FCC_FORM_REIM_SPLIT) st = prepare_reim(p);
         if (st != FCC_OK) {
             free_plan(p);
             return st;
         }
-    } else if (p->kh) {
-        st = choose_fp32_geometry(p);
-        if (st == FCC_OK) st = set_fp32_geometry(p, p->geo);
+    } else if (in.form == FCC_FORM_REIM_SPLIT) {
+        st = set_fp32_geometry(p, Fp32Geometry{});  // placeholder tables: more bases than any kernel takes
         if (st != FCC_OK) {
             free_plan(p);
             return st;

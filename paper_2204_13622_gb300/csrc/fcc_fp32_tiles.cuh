@@ -1,0 +1,572 @@
+// fcc_fp32_tiles.cuh -- the per-tile pipeline of the FP32 FCC kernels (stage,
+// per-microphone PHAT and folded re-lay, cross spectra + projection,
+// reduce-scatter, reconstruction + argmax + refinement), shared by the folded
+// kernels (fcc_fp32.cu) and the split-form kernel (fcc_fp32_reim.cu).
+#pragma once
+
+#include <cfloat>
+
+#include "fcc_device.cuh"
+#include "fcc_internal.h"
+
+namespace fcc {
+namespace {
+
+constexpr int kMaxRowSlots = 8;                  // fold records per lane per row (RS): N <= 1024
+
+// Registers are split per SM sub-partition (16K each), so the warp count and
+// the register cap must fit together: KH >= 6 keeps up to 255 registers with 8
+// warps; smaller KH caps registers at 168 with 12 warps.
+__host__ __device__ constexpr int max_compute_warps(int kh) { return kh >= 6 ? 8 : 12; }
+
+
+struct SmemLayout {
+    size_t bar_off, slot_off, basis_off, recon_off, stage_off, stage_bytes, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int S, int n_slots, int Q, int kh, int C, int BS, int center,
+                                                  int F, int frame_bytes)
+{
+    SmemLayout L;
+    size_t o = 0;
+    L.bar_off = o;
+    o += 3 * (size_t)S * 8;
+    o = (o + 15) & ~(size_t)15;
+    L.slot_off = o;
+    o += (size_t)n_slots * sizeof(Slot);
+    o = (o + 15) & ~(size_t)15;
+    L.basis_off = o;
+    o += (size_t)(Q + C + 1) * BS * sizeof(float);
+    o = (o + 15) & ~(size_t)15;
+    L.recon_off = o;
+    o += (size_t)(center + 1) * 4 * kh * sizeof(float);
+    o = (o + 127) & ~(size_t)127;
+    L.stage_off = o;
+    L.stage_bytes = (((size_t)F * frame_bytes) + 127) & ~(size_t)127;
+    o += (size_t)S * L.stage_bytes;
+    L.total = o;
+    return L;
+}
+
+
+// Byte offsets, inside a tile, of row R's fold records and of its lone bin N/4.
+__device__ __forceinline__ int rec_off(int R, int B) { return R * B * 8 + ((R & 1) ? 8 : 0); }
+__device__ __forceinline__ int lone_off(int R, int B, int Q) { return R * B * 8 + ((R & 1) ? 0 : 16 * Q); }
+
+
+// The whole per-tile pipeline for one plan: this CTA processes tiles
+// tile_base + k * tile_stride, k = 0 .. n_local - 1, with the geometry and tables
+// of `p` laid out from `smem`.  Warps beyond the plan's G * GW only help load the
+// tables.  Every barrier this call initialises is idle again when it returns
+// (all copies it issued have landed).
+// RS = fold records per lane per row = max(1, N / 128) (N/4 records over 32 lanes).
+// FB = the split form (cosine bases on Re x, sine bases on Im x, Eq. 3 without
+// the Eq. 8 fold): the same records feed 2 KH coefficient pairs (c_v, s_v),
+// accE holding v < KH and accO holding KH + v, and the reconstruction table
+// holds (2 U_c, 2 U_s) so that the same S -/+ D evaluation gives
+// y(+/-tau) = 2 (U_c c -/+ U_s s).
+template <int KH, int RS, bool FB>
+__device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *smem, long long tile_base,
+                                           long long tile_stride, int n_local)
+{
+    const int frame_bytes = p.frame_floats * 4;
+    const SmemLayout lay = smem_layout(p.S, p.n_slots, p.Q, KH, p.C, p.BS, p.center, p.F, frame_bytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + lay.bar_off);
+    uint64_t *normd = full + p.S;   // group: every row of the tile re-laid
+    uint64_t *freed = normd + p.S;  // group: every warp left the tile's rows
+    Slot *slots = reinterpret_cast<Slot *>(smem + lay.slot_off);
+    float *basis = reinterpret_cast<float *>(smem + lay.basis_off);
+    float *recon = reinterpret_cast<float *>(smem + lay.recon_off);
+    unsigned char *stages = smem + lay.stage_off;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group = warp / p.GW, wig = warp - group * p.GW;
+    const bool member = group < p.G;  // this warp belongs to one of the plan's groups
+    const bool leader = member && wig == 0 && lane == 0;
+
+    // ---- prologue: barriers, tables into shared memory
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < p.S; ++s) {
+            mbar_init(&full[s], p.bulk ? 1u : (unsigned)(p.GW * 32));
+            mbar_init(&normd[s], (unsigned)p.GW);
+            mbar_init(&freed[s], (unsigned)p.GW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
+    for (int e = threadIdx.x; e < (p.Q + p.C + 1) * p.BS; e += blockDim.x) basis[e] = p.basis[e];
+    for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
+    fence_proxy_async();
+    __syncthreads();
+
+    auto tile_src = [&](int k, int &nf) {
+        const long long tile = tile_base + (long long)k * tile_stride;
+        const long long f0 = tile * p.F;
+        nf = (int)min((long long)p.F, p.T - f0);
+        return f0;
+    };
+    // Issue the bulk copy of this CTA's tile k into its stage (group leader only).
+    auto issue = [&](int k) {
+        int nf;
+        const long long f0 = tile_src(k, nf);
+        const int s = k % p.S;
+        const unsigned bytes = (unsigned)nf * (unsigned)frame_bytes;
+        mbar_arrive_expect_tx(&full[s], bytes);
+        bulk_g2s(stages + (size_t)s * lay.stage_bytes,
+                 reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes, bytes, &full[s]);
+    };
+
+    // prime this group's stages (the test hook withholds CTA 0's first copy, so
+    // that group's first wait runs out and the timeout path is taken)
+    const int Sg = p.S / p.G;
+    if (p.bulk && leader)
+        for (int j = 0; j < Sg; ++j)
+            if (group + j * p.G < n_local && !(p.inject && blockIdx.x == 0 && group == 0 && j == 0))
+                issue(group + j * p.G);
+
+    // lane -> (frame in tile, slot, chunk).  A frame takes n_blocks whole warps;
+    // inside a warp the lanes are chunk-major (lane = chunk * SB + slot), so the
+    // 32 / SB lanes of a quarter-warp share one chunk and read one basis row.
+    const int lane_g = wig * 32 + lane;
+    const int fl = lane_g / p.lanes_frame;
+    const int rem = lane_g - fl * p.lanes_frame;
+    const int chunk = (rem & 31) / p.SB;
+    const int slot_id = (rem >> 5) * p.SB + (rem & 31) % p.SB;
+    const int QC = p.Q / p.C;
+    const int B = p.B, Q = p.Q, M = p.M;
+    const unsigned FULLM = 0xffffffffu;
+    int k_done = group - p.G;  // last tile fully consumed by this group
+
+    for (int k = group; member && k < n_local; k += p.G) {
+        const int s = k % p.S;
+        const unsigned par = (unsigned)(k / p.S) & 1u;
+        int nf;
+        const long long f0 = tile_src(k, nf);
+        unsigned char *st = stages + (size_t)s * lay.stage_bytes;
+        if (!p.bulk) {
+            // plain-load staging (frame size not a multiple of 16 bytes)
+            const size_t n8 = (size_t)nf * frame_bytes / 8;
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(
+                reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(st);
+            for (size_t e = lane_g; e < n8; e += p.GW * 32) dst[e] = __ldg(src + e);
+            mbar_arrive(&full[s]);
+        }
+        if (!mbar_wait(&full[s], par, p.wait_cycles)) {
+            if (lane == 0) atomicOr(p.err, kErrTimeout);
+            break;
+        }
+
+        // ---- 2. PHAT + folded re-lay, one row per warp at a time
+        {
+            bool bad = false;
+            const int rows = nf * M;
+            for (int R = wig; R < rows; R += p.GW) {
+                const float2 *raw = reinterpret_cast<const float2 *>(st + (size_t)R * B * 8);
+                float2 a[RS], b[RS], lone = make_float2(0.f, 0.f);
+                bool ok = true;
+#pragma unroll
+                for (int j = 0; j < RS; ++j) {
+                    const int fp = lane + 32 * j;
+                    if (RS > 1 || fp < Q) {
+                        bool o1, o2;
+                        a[j] = unit_phase_fast(raw[fp], o1);
+                        b[j] = unit_phase_fast(raw[2 * Q - fp], o2);
+                        ok = ok && o1 && o2;
+                    }
+                }
+                if (lane == 0) {
+                    bool o;
+                    lone = unit_phase_fast(raw[Q], o);
+                    ok = ok && o;
+                }
+                if (!__all_sync(FULLM, ok)) {  // rare: zero, tiny, huge or non-finite bins
+#pragma unroll
+                    for (int j = 0; j < RS; ++j) {
+                        const int fp = lane + 32 * j;
+                        if (RS > 1 || fp < Q) {
+                            a[j] = unit_phase_slow(raw[fp], bad);
+                            b[j] = unit_phase_slow(raw[2 * Q - fp], bad);
+                        }
+                    }
+                    if (lane == 0) lone = unit_phase_slow(raw[Q], bad);
+                }
+                __syncwarp();  // the whole row is read before any of it is rewritten
+                float4 *recs = reinterpret_cast<float4 *>(st + rec_off(R, B));
+                const int sw = rec_swz(R, Q);
+#pragma unroll
+                for (int j = 0; j < RS; ++j) {
+                    const int fp = lane + 32 * j;
+                    if (RS > 1 || fp < Q) recs[fp ^ sw] = make_float4(a[j].x, a[j].y, b[j].x, b[j].y);
+                }
+                if (lane == 0) *reinterpret_cast<float2 *>(st + lone_off(R, B, Q)) = lone;
+                __syncwarp();
+            }
+            if (__any_sync(FULLM, bad) && lane == 0) atomicOr(p.err, kErrNonFinite);
+        }
+        if (p.GW > 1) {
+            if (lane == 0) mbar_arrive(&normd[s]);
+            if (!mbar_wait(&normd[s], par, p.wait_cycles)) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+        }
+
+        // ---- 3. fold + projection over this lane's chunk of bin pairs
+        const bool active = (fl < nf) && (slot_id < p.n_slots);
+        f2 accE[4][KH], accO[4][KH];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int v = 0; v < KH; ++v) accE[q][v] = accO[q][v] = 0ull;
+        Slot sl{};
+        if (active) {
+            sl = slots[slot_id];
+            const int R0 = fl * M;
+            const float4 *bas = reinterpret_cast<const float4 *>(basis);
+            // basis row stride in float4 (odd): folded KH even + KH odd weights;
+            // split form 2 KH coefficient rows of (C(f), S(f), C(N/2-f), S(N/2-f))
+            constexpr int BS4 = FB ? 2 * KH + 1 : (((KH / 2) % 2 == 0) ? KH / 2 + 1 : KH / 2);
+            const float4 *bchunk = bas + (size_t)chunk * (QC + 1) * BS4;  // one pad row per chunk
+            auto body = [&](const float4 (&X)[2], const float4 (&Y)[2], const float4 *brow) {
+                // packed operands: x as (re, im) and swapped (im, re) per X microphone
+                // and bin, y as (re, re) and (im, -im) per Y microphone and bin, so
+                // that x y^* = (xr yr + xi yi, xi yr - xr yi) is one FMUL2 + one FFMA2
+                f2 xa[2][2], xw[2][2], yr[2][2], yi[2][2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    xa[u][0] = pk(X[u].x, X[u].y);
+                    xw[u][0] = pk(X[u].y, X[u].x);
+                    xa[u][1] = pk(X[u].z, X[u].w);
+                    xw[u][1] = pk(X[u].w, X[u].z);
+                    yr[u][0] = pk(Y[u].x, Y[u].x);
+                    yi[u][0] = pk(Y[u].y, -Y[u].y);
+                    yr[u][1] = pk(Y[u].z, Y[u].z);
+                    yi[u][1] = pk(Y[u].w, -Y[u].w);
+                }
+                if constexpr (FB) {
+                    // cross spectra of the four pairs at f and N/2 - f, then per
+                    // coefficient v: (c_v, s_v) += (C_v, S_v) (Re, Im) at both bins
+                    f2 a[4], b[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ix = q >> 1, iy = q & 1;
+                        a[q] = fma2(xw[ix][0], yi[iy][0], mul2(xa[ix][0], yr[iy][0]));
+                        b[q] = fma2(xw[ix][1], yi[iy][1], mul2(xa[ix][1], yr[iy][1]));
+                    }
+#pragma unroll
+                    for (int v = 0; v < KH; ++v) {
+                        const float4 e = brow[v], o = brow[KH + v];
+                        const f2 ef = pk(e.x, e.y), eg = pk(e.z, e.w), of = pk(o.x, o.y), og = pk(o.z, o.w);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            accE[q][v] = fma2(eg, b[q], fma2(ef, a[q], accE[q][v]));
+                            accO[q][v] = fma2(og, b[q], fma2(of, a[q], accO[q][v]));
+                        }
+                    }
+                } else {
+                    f2 bE[KH], bO[KH];
+                    float w[2 * KH];
+#pragma unroll
+                    for (int v = 0; v < KH / 2; ++v) {
+                        const float4 e = brow[v];
+                        w[4 * v] = e.x;
+                        w[4 * v + 1] = e.y;
+                        w[4 * v + 2] = e.z;
+                        w[4 * v + 3] = e.w;
+                    }
+#pragma unroll
+                    for (int v = 0; v < KH; ++v) {
+                        bE[v] = pk(w[v], w[v]);
+                        bO[v] = pk(w[KH + v], w[KH + v]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ix = q >> 1, iy = q & 1;
+                        // cross spectra at f and N/2 - f: a = x(f) y(f)^*, b = x(N/2-f) y(N/2-f)^*
+                        const f2 a = fma2(xw[ix][0], yi[iy][0], mul2(xa[ix][0], yr[iy][0]));
+                        const f2 b = fma2(xw[ix][1], yi[iy][1], mul2(xa[ix][1], yr[iy][1]));
+                        const f2 xs = add2(a, b), xd = sub2(a, b);  // Eq. 8
+#pragma unroll
+                        for (int v = 0; v < KH; ++v) {
+                            accE[q][v] = fma2(bE[v], xs, accE[q][v]);
+                            accO[q][v] = fma2(bO[v], xd, accO[q][v]);
+                        }
+                    }
+                }
+            };
+            const int cb = chunk * QC;
+            const int st_off = (int)(st - smem);
+            // Each lane takes its slot's microphones in the order of its role in
+            // the reduce-scatter: chunk bit 1 swaps the two X microphones, chunk
+            // bit 0 the two Y microphones, so accumulator q always holds the pair
+            // this lane keeps (q = 0) or hands on, with no selects.
+            const int sx = (chunk >> 1) & 1, sy = chunk & 1;
+            const int mr[4] = {sx ? sl.mic[1] : sl.mic[0], sx ? sl.mic[0] : sl.mic[1],
+                               sy ? sl.mic[3] : sl.mic[2], sy ? sl.mic[2] : sl.mic[3]};
+            int sw[4], rb[4];  // byte offsets from the shared-memory base
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sw[r] = rec_swz(R0 + mr[r], Q);
+                rb[r] = st_off + rec_off(R0 + mr[r], B) + 16 * cb;
+            }
+            if ((QC & 7) == 0) {
+                // 8 records at a time: record cb+t8+j of a swizzled row is at
+                // cb+t8+(j^4), i.e. +4 records for j < 4 and -4 for j >= 4
+                int lo[4], hi[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    lo[r] = rb[r] + 16 * sw[r];
+                    hi[r] = rb[r] - 16 * sw[r];
+                }
+                // two 8-record blocks per iteration pay for KH = 8 (16-mic grid: 8 %
+                // faster) and cost the 4-basis kernels (8-mic circle: 11 % slower)
+                constexpr int kBlockUnroll = KH >= 8 ? 2 : 1;
+#pragma unroll kBlockUnroll
+                for (int t8 = 0; t8 < QC; t8 += 8) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int o = 16 * (t8 + j);
+                        float4 X[2], Y[2];
+                        X[0] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[0] : hi[0]) + o);
+                        X[1] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[1] : hi[1]) + o);
+                        Y[0] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[2] : hi[2]) + o);
+                        Y[1] = *reinterpret_cast<const float4 *>(smem + (j < 4 ? lo[3] : hi[3]) + o);
+                        body(X, Y, bchunk + (size_t)(t8 + j) * BS4);
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int t = 0; t < QC; ++t) {
+                    float4 X[2], Y[2];
+                    X[0] = *reinterpret_cast<const float4 *>(smem + rb[0] + 16 * (((cb + t) ^ sw[0]) - cb));
+                    X[1] = *reinterpret_cast<const float4 *>(smem + rb[1] + 16 * (((cb + t) ^ sw[1]) - cb));
+                    Y[0] = *reinterpret_cast<const float4 *>(smem + rb[2] + 16 * (((cb + t) ^ sw[2]) - cb));
+                    Y[1] = *reinterpret_cast<const float4 *>(smem + rb[3] + 16 * (((cb + t) ^ sw[3]) - cb));
+                    body(X, Y, bchunk + (size_t)t * BS4);
+                }
+            }
+            if (chunk == 0) {
+                // bin N/4: x_s = R_hat(N/4); the odd bases vanish there (Eq. 8)
+                float2 X[2], Y[2];
+                X[0] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[0], B, Q));
+                X[1] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[1], B, Q));
+                Y[0] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[2], B, Q));
+                Y[1] = *reinterpret_cast<const float2 *>(st + lone_off(R0 + sl.mic[3], B, Q));
+                const float4 *brow = bas + (size_t)p.C * (QC + 1) * BS4;
+                if constexpr (FB) {
+                    // split form: row v holds (C_v(N/4), S_v(N/4), 0, 0)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 x = X[q >> 1], y = Y[q & 1];
+                        const f2 xs = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
+#pragma unroll
+                        for (int v = 0; v < KH; ++v) {
+                            const float4 e = brow[v], o = brow[KH + v];
+                            accE[q][v] = fma2(pk(e.x, e.y), xs, accE[q][v]);
+                            accO[q][v] = fma2(pk(o.x, o.y), xs, accO[q][v]);
+                        }
+                    }
+                } else {
+                    f2 bE[KH];
+#pragma unroll
+                    for (int v = 0; v < KH / 4 + (KH % 4 ? 1 : 0); ++v) {
+                        const float4 e = brow[v];
+                        if (4 * v < KH) bE[4 * v] = pk(e.x, e.x);
+                        if (4 * v + 1 < KH) bE[4 * v + 1] = pk(e.y, e.y);
+                        if (4 * v + 2 < KH) bE[4 * v + 2] = pk(e.z, e.z);
+                        if (4 * v + 3 < KH) bE[4 * v + 3] = pk(e.w, e.w);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 x = X[q >> 1], y = Y[q & 1];
+                        const f2 xs = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
+#pragma unroll
+                        for (int v = 0; v < KH; ++v) accE[q][v] = fma2(bE[v], xs, accE[q][v]);
+                    }
+                }
+            }
+        }
+        // ---- release the stage and refill it with this group's tile k + S
+        fence_proxy_async();  // our generic writes precede the next bulk write
+        __syncwarp();
+        if (p.bulk) {
+            if (p.GW > 1) {
+                if (lane == 0) mbar_arrive(&freed[s]);
+                if (leader && k + p.S < n_local) {
+                    if (!mbar_wait(&freed[s], par, p.wait_cycles)) {
+                        atomicOr(p.err, kErrTimeout);
+                    } else {
+                        issue(k + p.S);
+                    }
+                }
+            } else if (lane == 0 && k + p.S < n_local) {
+                issue(k + p.S);
+            }
+        } else if (p.GW > 1) {
+            // plain staging: the group's next copy must not start before every
+            // warp has left this stage
+            if (lane == 0) mbar_arrive(&freed[s]);
+            if (!mbar_wait(&freed[s], par, p.wait_cycles)) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+        }
+        k_done = k;
+
+        // ---- 4. reduce-scatter of the chunk partials: lane (chunk & 3) keeps pair (chunk & 3)
+        f2 zE[KH], zO[KH];
+        {
+            // level 1 (lanes 2 SB apart): keep accumulators 0, 1, hand on 2, 3
+            f2 rE[2][KH], rO[2][KH];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int v = 0; v < KH; ++v) {
+                    float m0, m1, o0, o1;
+                    upk(accE[pp][v], m0, m1);
+                    upk(accE[pp + 2][v], o0, o1);
+                    rE[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
+                    upk(accO[pp][v], m0, m1);
+                    upk(accO[pp + 2][v], o0, o1);
+                    rO[pp][v] = pk(m0 + __shfl_xor_sync(FULLM, o0, 2 * p.SB), m1 + __shfl_xor_sync(FULLM, o1, 2 * p.SB));
+                }
+            // level 2 (lanes SB apart): keep 0, hand on 1; then plain sums over the other chunks
+#pragma unroll
+            for (int v = 0; v < KH; ++v) {
+                float m0, m1, o0, o1;
+                upk(rE[0][v], m0, m1);
+                upk(rE[1][v], o0, o1);
+                float e0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), e1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
+                upk(rO[0][v], m0, m1);
+                upk(rO[1][v], o0, o1);
+                float d0 = m0 + __shfl_xor_sync(FULLM, o0, p.SB), d1 = m1 + __shfl_xor_sync(FULLM, o1, p.SB);
+                for (int o = 4 * p.SB; o < 32; o <<= 1) {
+                    e0 += __shfl_xor_sync(FULLM, e0, o);
+                    e1 += __shfl_xor_sync(FULLM, e1, o);
+                    d0 += __shfl_xor_sync(FULLM, d0, o);
+                    d1 += __shfl_xor_sync(FULLM, d1, o);
+                }
+                zE[v] = pk(e0, e1);
+                zO[v] = pk(d0, d1);
+            }
+        }
+
+        // ---- 5. reconstruction on the grid, argmax, peak, refinement
+        const int q = chunk & 3;
+        const int pq = q == 0 ? sl.pair[0] : q == 1 ? sl.pair[1] : q == 2 ? sl.pair[2] : sl.pair[3];
+        // The pair's y(tau) values at bi - 1 and bi + 1 (FP64 differences) give the
+        // three-point parabola; the coefficients go out when asked for.
+        auto emit = [&](size_t o, int bi, float best) {
+            p.out_idx[o] = bi;
+            p.out_peak[o] = best;
+            if (p.out_tau) {
+                float off = 0.f;
+                if (bi > 0 && bi < p.I - 1) {
+                    // three-point parabola; the differences, where the
+                    // cancellation happens, are exact in FP64
+                    const double y_m = y_at<KH>(recon, p.center, bi - 1, zE, zO);
+                    const double y_p = y_at<KH>(recon, p.center, bi + 1, zE, zO);
+                    const double num = y_m - y_p;
+                    const double den = (y_m - 2.0 * (double)best) + y_p;
+                    if (den < 0.0) off = fminf(0.5f, fmaxf(-0.5f, 0.5f * (float)num / (float)den));
+                }
+                p.out_tau[o] = ((float)(bi - p.center) + off) * p.delta;
+            }
+            if (!FB && p.out_coef) {  // the split form has no coefficient output
+                const int K = p.KE + p.KO;
+                float *cf = p.out_coef + o * 2 * K;
+#pragma unroll
+                for (int v = 0; v < KH; ++v) {
+                    float a, b;
+                    if (v < p.KE) {
+                        upk(zE[v], a, b);
+                        cf[v] = a;
+                        cf[p.KE + v] = b;
+                    }
+                    if (v < p.KO) {
+                        upk(zO[v], a, b);
+                        cf[2 * p.KE + v] = a;
+                        cf[2 * p.KE + p.KO + v] = b;
+                    }
+                }
+            }
+        };
+        // One outward scan over lag steps m = m0, m0 + stride, ...: y(center - m)
+        // is below every index this lane has seen (wins ties), y(center + m)
+        // above every one (loses ties).
+        auto scan = [&](int m0, int stride, float &best, int &bi, float *corr) {
+            float S, D;
+            for (int m = m0; m <= p.center; m += stride) {
+                eval_SD<KH>(recon, m, zE, zO, S, D);
+                const float ym = S + D, yp = S - D;  // y(center - m), y(center + m)
+                if (ym >= best) {
+                    best = ym;
+                    bi = p.center - m;
+                }
+                if (yp > best) {
+                    best = yp;
+                    bi = p.center + m;
+                }
+                if (corr) {
+                    corr[p.center - m] = ym;
+                    corr[p.center + m] = yp;
+                }
+            }
+        };
+        if (p.C == 4) {
+            // one chunk lane per pair
+            if (active && pq >= 0) {
+                const size_t o = (size_t)(f0 + fl) * p.P + pq;
+                float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
+                float S, D;
+                eval_SD<KH>(recon, 0, zE, zO, S, D);
+                float best = S - D;
+                int bi = p.center;
+                if (corr) corr[p.center] = best;
+                scan(1, 1, best, bi, corr);
+                emit(o, bi, best);
+            }
+        } else {
+            // the C / 4 chunk lanes holding the same pair (the reduction leaves
+            // its coefficients in all of them) split the lag steps m = gi,
+            // gi + C/4, ... and combine their maxima with shuffles: value first,
+            // then the lower lag index, as one outward scan would
+            const int G4 = p.C >> 2, gi = chunk >> 2;
+            const bool mine = active && pq >= 0;
+            const size_t o = mine ? (size_t)(f0 + fl) * p.P + pq : 0;
+            float best = -FLT_MAX;
+            int bi = 0x7fffffff;
+            if (mine) {
+                float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
+                int m0 = gi;
+                if (gi == 0) {
+                    float S, D;
+                    eval_SD<KH>(recon, 0, zE, zO, S, D);
+                    best = S - D;
+                    bi = p.center;
+                    if (corr) corr[p.center] = best;
+                    m0 = G4;
+                }
+                scan(m0, G4, best, bi, corr);
+            }
+            for (int off = 4 * p.SB; off < 32; off <<= 1) {
+                const float ob = __shfl_xor_sync(FULLM, best, off);
+                const int oi = __shfl_xor_sync(FULLM, bi, off);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (mine && gi == 0) emit(o, bi, best);
+        }
+    }
+    // never retire with one of this group's bulk copies still in flight
+    if (p.bulk && leader) {
+        for (int k = k_done + p.G; k < n_local && k <= k_done + p.S; k += p.G)
+            if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u, p.wait_cycles)) atomicOr(p.err, kErrTimeout);
+    }
+}
+
+}  // namespace
+}  // namespace fcc

@@ -210,16 +210,14 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
 fcc_status_t prepare_tc(fcc_plan *plan);
 fcc_status_t launch_tc(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                        float *tau, float *coef, float *corr, cudaStream_t st);
-// Split-form (FCC_FORM_REIM_SPLIT) tables for the per-pair kernel, and its launch
-// for alpha = 1 (no recursion state).
+// Split-form (FCC_FORM_REIM_SPLIT) weights of the per-pair kernel (Eq. 1
+// smoothing), and the split-form FP32 kernel's launch (alpha = 1).
 fcc_status_t prepare_reim(fcc_plan *plan);
-fcc_status_t launch_reim(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak, float *tau,
-                         float *coef, float *corr, cudaStream_t st);
-// FP32 or tensor-core path, by the plan's form and precision.
+fcc_status_t launch_fp32_reim(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid);
+// FP32 (folded or split form) or tensor-core path, by the plan's precision.
 inline fcc_status_t launch_tdoa(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                                 float *tau, float *coef, float *corr, cudaStream_t st)
 {
-    if (plan->info.form == FCC_FORM_REIM_SPLIT) return launch_reim(plan, spectra, T, idx, peak, tau, coef, corr, st);
     return plan->info.prec == FCC_PREC_FP32 ? launch_fp32(plan, spectra, T, idx, peak, tau, coef, corr, st)
                                             : launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
 }

@@ -496,7 +496,7 @@ bool is_split(const fcc_plan *plan) { return plan->info.form == FCC_FORM_REIM_SP
 fcc_status_t smooth_geometry(const fcc_plan *plan, long long T, SmoothPlan &g)
 {
     const fcc_plan_info_t &in = plan->info;
-    const char *what = is_split(plan) ? "the split form" : "the smoothed path";
+    const char *what = is_split(plan) ? "the smoothed split form" : "the smoothed path";
     if (in.prec != FCC_PREC_FP32) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " is FP32");
     if (in.M % 2) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " needs an even number of mics");
     if (plan->n_slots > 8) return fail(FCC_ERR_UNSUPPORTED, std::string(what) + " needs at most 8 mics");
@@ -628,15 +628,14 @@ fcc_status_t run_per_pair(const fcc_plan *plan, const SmoothPlan &g, const float
 
 }  // namespace
 
-// Split-form tables for the per-pair kernel, built once when the plan is
-// created: weights [2 KH][2Q + 4] of (cosine, sine) pairs (sigma v_k of C and
-// of S over bins 0..N/2, zero past K_c / K_s and in the padding), and the
-// reconstruction table [center + 1][KH][4] = (2 U_c[k], 2 U_s[k], 2 U_c[KH + k],
-// 2 U_s[KH + k]) at tau = +m / den, which replaces the folded table.
+// Split-form weights for the per-pair kernel (Eq. 1 smoothing), built once when
+// the plan is created: [2 KH][2Q + 4] (cosine, sine) pairs, sigma v_k of C and
+// of S over bins 0..N/2, zero past K_c / K_s and in the padding.  The
+// reconstruction table is the FP32 kernel's split-form table (pack_tables).
 fcc_status_t prepare_reim(fcc_plan *plan)
 {
     const fcc_plan_info_t &in = plan->info;
-    const int kh = plan->kh, B = in.B, Kc = in.K_even, Ks = in.K_odd, I = in.I;
+    const int kh = plan->kh, B = in.B, Kc = in.K_even, Ks = in.K_odd;
     const SmoothLayout Ly(in.Q, kh, in.center, in.M, in.B, std::max(plan->n_slots, 1), true);
     std::vector<float> w((size_t)2 * kh * Ly.QP * 2, 0.f);
     for (int k = 0; k < 2 * kh; ++k)
@@ -644,46 +643,16 @@ fcc_status_t prepare_reim(fcc_plan *plan)
             w[((size_t)k * Ly.QP + f) * 2] = k < Kc ? (float)plan->Pe[(size_t)k * B + f] : 0.f;
             w[((size_t)k * Ly.QP + f) * 2 + 1] = k < Ks ? (float)plan->Po[(size_t)k * B + f] : 0.f;
         }
-    std::vector<float> rec((size_t)(in.center + 1) * 4 * kh, 0.f);
-    auto uc = [&](int i, int k) { return k < Kc ? plan->Ue[(size_t)i * Kc + k] : 0.0; };
-    auto us = [&](int i, int k) { return k < Ks ? plan->Uo[(size_t)i * Ks + k] : 0.0; };
-    for (int m = 0; m <= in.center; ++m) {
-        const int i = in.center + m;
-        (void)I;
-        for (int k = 0; k < kh; ++k) {
-            float *g = &rec[((size_t)m * kh + k) * 4];
-            g[0] = (float)(2.0 * uc(i, k));
-            g[1] = (float)(2.0 * us(i, k));
-            g[2] = (float)(2.0 * uc(i, kh + k));
-            g[3] = (float)(2.0 * us(i, kh + k));
-        }
-    }
-    float *dw = nullptr, *dr = nullptr;
+    float *dw = nullptr;
     cudaError_t e = dev_alloc((void **)&dw, w.size() * sizeof(float));
-    if (e == cudaSuccess) e = dev_alloc((void **)&dr, rec.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(dw, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dr, rec.data(), rec.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dw);
-        cudaFree(dr);
-        return cuda_fail(e, "split-form tables");
+        return cuda_fail(e, "split-form per-pair weights");
     }
     cudaFree(plan->d_smooth_basis);
-    cudaFree(plan->d_recon);
     plan->d_smooth_basis = dw;
-    plan->d_recon = dr;
     return FCC_OK;
-}
-
-fcc_status_t launch_reim(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak, float *tau,
-                         float *coef, float *corr, cudaStream_t st)
-{
-    if (coef || corr) return fail(FCC_ERR_UNSUPPORTED, "the split form has no coefficient or correlation output");
-    SmoothPlan g{};
-    fcc_status_t s = smooth_geometry(plan, std::max<long long>(T, 1), g);
-    if (s != FCC_OK) return s;
-    if (T == 0) return FCC_OK;
-    return run_per_pair(plan, g, spectra, T, 1.f, 0.f, nullptr, idx, peak, tau, nullptr, st);
 }
 
 }  // namespace fcc

@@ -88,11 +88,12 @@ def test_allocation_failure_during_plan_creation(hooks):
     plan.close()
 
 
-@pytest.mark.parametrize("form,alpha", [("folded", 0.1), ("reim", 1.0)])
+@pytest.mark.parametrize("form,alpha", [("folded", 0.1), ("reim", 0.5), ("reim", 1.0)])
 def test_per_pair_kernel_timeout_path(hooks, form, alpha):
-    # the per-pair kernel (smoothed path; split form) takes the same exit: its
-    # first frame withheld in CTA 0, a short wait bound, FCC_ERR_TIMEOUT, and the
-    # next launch on the same context equal to the reference
+    # the per-pair kernel (smoothed path, both forms) and the split-form FP32
+    # kernel (alpha = 1) take the same exit: the first copy withheld in CTA 0, a
+    # short wait bound, FCC_ERR_TIMEOUT, and the next launch on the same context
+    # equal to the reference
     B = hooks
     plan = B.Plan(8, 16000.0, 512, 4, tau_max=5, form=form)
     X = _spectra(3000, 8, 2)

@@ -1,9 +1,10 @@
 """GPU parity of the split form (FCC_FORM_REIM_SPLIT: cosine bases on Re x,
 sine bases on Im x, each truncated by its own SVD) against the oracle's form B
-(oracle.BasisB: y = 2 Re{(C_K + j S_K) x}), for alpha = 1 (fcc_tdoa) and
-alpha < 1 (fcc_tdoa_smoothed).  Tolerances as the FP32 path (tests/helpers.py):
-peaks within 1e-4 of the pair-frame's max |y|, argmax exact where the oracle's
-top-2 gap is clear."""
+(oracle.BasisB: y = 2 Re{(C_K + j S_K) x}), for alpha = 1 (fcc_tdoa, the FP32
+tile kernel: any M, N <= 1024) and alpha < 1 (fcc_tdoa_smoothed, the per-pair
+kernel).  Tolerances as the FP32 path (tests/helpers.py): peaks and
+correlations within 1e-4 of the pair-frame's max |y|, argmax exact where the
+oracle's top-2 gap is clear."""
 import numpy as np
 import pytest
 
@@ -44,15 +45,20 @@ def _check(out, ref):
 
 
 @pytest.mark.parametrize("M,N,den,L,T", [(8, 512, 4, 5, 211), (4, 256, 4, 3, 150), (2, 128, 2, 2, 97),
-                                         (6, 512, 8, 2, 64)])
+                                         (6, 512, 8, 2, 64), (5, 1024, 4, 3, 40), (3, 64, 2, 2, 53),
+                                         (16, 256, 4, 2, 30), (7, 512, 4, 12, 19)])
 def test_split_form_matches_oracle(B, O, M, N, den, L, T):
     plan = B.Plan(M, 16000.0, N, den, tau_max=L, form="reim")
     ob = O.BasisB(N, L, den)
     assert (plan.K_even, plan.K_odd) == (ob.Kc, ob.Ks)
     X = _spectra(T, M, N, seed=M + T)
-    out = plan.tdoa(torch.from_numpy(X).cuda())
+    out = plan.tdoa(torch.from_numpy(X).cuda(), corr=True)
     plan.sync()
-    _check(out, O.tdoa(X, ob.WK, ob.taus, ob.delta, want_y=True))
+    ref = O.tdoa(X, ob.WK, ob.taus, ob.delta, want_y=True)
+    _check(out, ref)
+    y = ref[3]
+    scale = np.abs(y).max(-1, keepdims=True)
+    assert np.all(np.abs(out["corr"].cpu().numpy() - y) <= 1e-4 * scale)
     # the plan's FP64 bases give the same truncated C and S as the oracle's
     Pe, Po, Ue, Uo = plan.bases()
     assert np.abs(Ue @ Pe - ob.CK).max() < 1e-9 and np.abs(Uo @ Po - ob.SK).max() < 1e-9
@@ -79,9 +85,15 @@ def test_split_form_options(B):
         plan.tdoa(X, coeffs=True)
     assert e.value.status == 2
     with pytest.raises(B.FccError):
-        plan.tdoa(X, corr=True)
+        plan.tdoa_smoothed(X, 0.5, coeffs=True)
     with pytest.raises(B.FccError):
         plan.autotune(max_candidates=1)
+    # alpha = 1 through the per-pair kernel (fcc_tdoa_smoothed) and through the
+    # FP32 tile kernel (fcc_tdoa): two kernels, one argmax where the top-2 gap is clear
+    a = plan.tdoa_smoothed(X, 1.0)
+    b = plan.tdoa(X, corr=True)
+    plan.sync()
+    check_argmax(a["lag_idx"].cpu().numpy(), b["corr"].cpu().numpy().astype(np.float64))
     # the PCM front-end runs on split-form plans too
     rng = np.random.default_rng(3)
     pcm = torch.from_numpy((rng.standard_normal((128 * 30 + 512, 4)) * 3000).astype(np.int16)).cuda()
