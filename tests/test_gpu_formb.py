@@ -105,3 +105,37 @@ def test_split_form_options(B):
     with pytest.raises(B.FccError) as e:
         B.Plan(4, 16000.0, 512, 4, tau_max=3, form="reim", prec="bf16")
     assert e.value.status == 2
+
+
+def test_split_form_doa(B, O):
+    # the fused spectra -> DoA call on a split-form plan: the same bytes as the
+    # correlations of fcc_tdoa searched separately, and the oracle's form B
+    # correlations searched by the oracle on a sample of frames
+    from paper_2204_13622_gb300 import synth
+    xyz = synth.circular_array(8, 0.05)
+    N, den, fs, c = 512, 4, 16000.0, 343.0
+    L = synth.lag_extent(xyz, fs)
+    plan = B.Plan(8, fs, N, den, mic_xyz=xyz, form="reim")
+    dirs = synth.fibonacci_directions(256)
+    doa = B.Doa(plan, xyz, dirs)
+    T = 3000
+    Xd = synth.stft_domain_spectra(T, xyz, fs, N, 128, seed=4, device="cuda")
+    out = doa.tdoa_doa(Xd, pairs=True)
+    ref = plan.tdoa(Xd, corr=True)
+    s = doa.search(ref["corr"])
+    plan.sync()
+    assert torch.equal(out["dir_idx"], s["dir_idx"]) and torch.equal(out["score"], s["score"])
+    assert torch.equal(out["lag_idx"], ref["lag_idx"]) and torch.equal(out["peak"], ref["peak"])
+    ob = O.BasisB(N, L, den)
+    sel = np.arange(0, T, 150)
+    _, _, _, y = O.tdoa(Xd[sel].cpu().numpy(), ob.WK, ob.taus, ob.delta, want_y=True)
+    ref_idx, _, scores = O.doa_srp(y, L, den, xyz, fs, c, dirs, want_scores=True)
+    got = out["dir_idx"][sel].cpu().numpy()
+    tol = 1e-4 * plan.P * np.abs(y).max()  # FP32 FCC + FP32 search against FP64 throughout
+    srt = np.sort(scores, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 2 * tol
+    assert np.array_equal(got[clear], ref_idx[clear])
+    rows = np.arange(len(sel))
+    assert np.all(scores[rows, ref_idx] - scores[rows, got] <= 2 * tol)
+    doa.close()
+    plan.close()
