@@ -190,6 +190,28 @@ fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g)
 
 namespace {
 
+// The host-streaming staging ring (fcc_tdoa_host), back to "not created".
+void free_staging(fcc_plan *p)
+{
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->d_stage[b]);
+        cudaFree(p->d_stage_idx[b]);
+        cudaFree(p->d_stage_peak[b]);
+        cudaFree(p->d_stage_tau[b]);
+        p->d_stage[b] = nullptr;
+        p->d_stage_idx[b] = nullptr;
+        p->d_stage_peak[b] = nullptr;
+        p->d_stage_tau[b] = nullptr;
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    p->copy_stream = nullptr;
+    for (auto &e : p->ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    p->stage_frames = 0;
+}
+
 void free_plan(fcc_plan *p)
 {
     if (!p) return;
@@ -202,15 +224,7 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_smooth_basis);
     cudaFree(p->d_stft_tab);
     pcm_destroy(p);
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(p->d_stage[b]);
-        cudaFree(p->d_stage_idx[b]);
-        cudaFree(p->d_stage_peak[b]);
-        cudaFree(p->d_stage_tau[b]);
-    }
-    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
-    for (auto &e : p->ev)
-        if (e) cudaEventDestroy(e);
+    free_staging(p);
     gcc_destroy(p);
     delete p;
 }
@@ -491,16 +505,27 @@ fcc_status_t fcc_tdoa_host(fcc_plan_t *plan, const void *h_spectra, long long T,
     if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
     const fcc_plan_info_t &in = plan->info;
     const size_t frame_bytes = (size_t)in.M * in.B * 8;
-    if (!plan->d_stage[0]) {
-        long long chunk = std::max<long long>(1, (256LL << 20) / (long long)frame_bytes);
-        for (int b = 0; b < 2; ++b) {
-            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage[b], chunk * frame_bytes));
-            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_idx[b], chunk * in.P * sizeof(int)));
-            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_peak[b], chunk * in.P * sizeof(float)));
-            FCC_CUDA_TRY(cudaMalloc(&plan->d_stage_tau[b], chunk * in.P * sizeof(float)));
+    if (!plan->stage_frames) {
+        // the staging ring, created on first use; stage_frames is set only once
+        // every part exists, and a failed creation frees the parts it made
+        const long long chunk = std::max<long long>(1, (256LL << 20) / (long long)frame_bytes);
+        cudaError_t e = cudaSuccess;
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = dev_alloc(&plan->d_stage[b], chunk * frame_bytes);
+            if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void **>(&plan->d_stage_idx[b]), chunk * in.P * sizeof(int));
+            if (e == cudaSuccess)
+                e = dev_alloc(reinterpret_cast<void **>(&plan->d_stage_peak[b]), chunk * in.P * sizeof(float));
+            if (e == cudaSuccess)
+                e = dev_alloc(reinterpret_cast<void **>(&plan->d_stage_tau[b]), chunk * in.P * sizeof(float));
         }
-        FCC_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
-        for (auto &ev : plan->ev) FCC_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking);
+        for (auto &ev : plan->ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            free_staging(plan);
+            return e == cudaErrorMemoryAllocation ? fail(FCC_ERR_OOM, "fcc_tdoa_host staging")
+                                                  : cuda_fail(e, "fcc_tdoa_host staging");
+        }
         plan->stage_frames = chunk;
     }
     cudaStream_t cs = static_cast<cudaStream_t>(stream);

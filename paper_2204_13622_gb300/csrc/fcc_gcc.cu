@@ -100,10 +100,8 @@ __global__ void gcc_gather_kernel(const float *__restrict__ out, long long t0, l
     }
 }
 
-fcc_status_t ensure_state(fcc_plan *plan, GccState *&gs)
+fcc_status_t build_state(fcc_plan *plan, GccState *&gs)
 {
-    gs = static_cast<GccState *>(plan->gcc_state);
-    if (gs) return FCC_OK;
     const fcc_plan_info_t &in = plan->info;
     gs = new GccState();
     plan->gcc_state = gs;
@@ -128,6 +126,20 @@ fcc_status_t ensure_state(fcc_plan *plan, GccState *&gs)
     if (cr != CUFFT_SUCCESS) return fail(FCC_ERR_CUDA, "cufftPlanMany failed (" + std::to_string((int)cr) + ")");
     gs->fft_ok = true;
     return FCC_OK;
+}
+
+// The plan's GCC workspace, created on first use; a failed creation frees what
+// it had allocated, so a later call starts again from nothing.
+fcc_status_t ensure_state(fcc_plan *plan, GccState *&gs)
+{
+    gs = static_cast<GccState *>(plan->gcc_state);
+    if (gs) return FCC_OK;
+    const fcc_status_t st = build_state(plan, gs);
+    if (st != FCC_OK) {
+        gcc_destroy(plan);
+        gs = nullptr;
+    }
+    return st;
 }
 
 }  // namespace
