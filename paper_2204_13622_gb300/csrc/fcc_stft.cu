@@ -429,14 +429,23 @@ fcc_status_t fcc_tdoa_pcm_host(fcc_plan_t *plan, const void *h_pcm, fcc_pcm_t ty
         ps = new (std::nothrow) PcmState;
         if (!ps) return fail(FCC_ERR_OOM, "host allocation");
         plan->pcm_state = ps;
-        for (int b = 0; b < 2; ++b) {
-            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_idx[b], (size_t)hc * in.P * sizeof(int)));
-            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_peak[b], (size_t)hc * in.P * sizeof(float)));
-            FCC_CUDA_TRY(dev_alloc((void **)&ps->d_tau[b], (size_t)hc * in.P * sizeof(float)));
+        // a failed creation frees what it made, so a later call starts again
+        cudaError_t e = cudaSuccess;
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = dev_alloc((void **)&ps->d_idx[b], (size_t)hc * in.P * sizeof(int));
+            if (e == cudaSuccess) e = dev_alloc((void **)&ps->d_peak[b], (size_t)hc * in.P * sizeof(float));
+            if (e == cudaSuccess) e = dev_alloc((void **)&ps->d_tau[b], (size_t)hc * in.P * sizeof(float));
         }
-        FCC_CUDA_TRY(dev_alloc((void **)&ps->d_spec, (size_t)std::min(hc, device_chunk(plan)) * in.M * in.B * 8));
-        FCC_CUDA_TRY(cudaStreamCreateWithFlags(&ps->copy, cudaStreamNonBlocking));
-        for (auto &e : ps->ev) FCC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (e == cudaSuccess)
+            e = dev_alloc((void **)&ps->d_spec, (size_t)std::min(hc, device_chunk(plan)) * in.M * in.B * 8);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps->copy, cudaStreamNonBlocking);
+        for (auto &ev : ps->ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            pcm_destroy(plan);
+            return e == cudaErrorMemoryAllocation ? fail(FCC_ERR_OOM, "fcc_tdoa_pcm_host staging")
+                                                  : cuda_fail(e, "fcc_tdoa_pcm_host staging");
+        }
     }
     if (ps->pcm_cap < pcm_bytes) {
         FCC_CUDA_TRY(cudaDeviceSynchronize());
