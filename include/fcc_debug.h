@@ -2,8 +2,8 @@
  * fcc_debug.h -- test hooks for the failure paths of the library.  The paper
  * has no counterpart; these exist so that tests can drive the error exits of
  * the kernels and of plan creation without faulting a GPU: every device-side
- * wait in the FP32 kernels (the folded-form kernel, its batched form, and the
- * per-pair kernel of the smoothed path and the split form) is a bounded loop
+ * wait in the FP32 kernels (the folded-form kernel, its batched form, the
+ * split-form kernel, and the per-pair kernel of the smoothed path) is a bounded loop
  * that, when it runs out, latches FCC_ERR_TIMEOUT in the plan's error word and
  * lets the kernel finish once its own copies have landed.
  *
@@ -28,8 +28,10 @@ enum {
      * reports FCC_ERR_TIMEOUT.  Only launches that stage with bulk copies (an
      * even number of microphones) are affected. */
     FCC_DEBUG_WITHHOLD_COPY = 1,
-    /* The next `value` device allocations made while creating a plan fail as if
-     * the device were out of memory (fcc_plan_create returns FCC_ERR_OOM). */
+    /* The next `value` device allocations made while creating a plan, or the
+     * staging of fcc_tdoa_host / fcc_tdoa_pcm_host on their first call, fail as
+     * if the device were out of memory (the call returns FCC_ERR_OOM and keeps
+     * nothing of what it had allocated). */
     FCC_DEBUG_FAIL_ALLOC = 2
 };
 
