@@ -12,7 +12,9 @@
  * chunks of frames: the recursion from zero inside each chunk, a carry scan
  * over the chunks, and the FCC pass that restarts every chunk from its carry.
  *
- * Supported plans: FP32, an even number of microphones up to 8, 128 <= N <= 512.
+ * Supported plans: FP32, an even number of microphones up to 8, 128 <= N <= 512,
+ * either form (FCC_FORM_REIM_SPLIT plans project R_hat on their cosine and sine
+ * bases instead of folding it, and take no d_coeffs).
  */
 #ifndef FCC_SMOOTH_GB300_H
 #define FCC_SMOOTH_GB300_H
