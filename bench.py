@@ -366,6 +366,9 @@ def run_fcc(args, rank, world, local):
     if rank == 0:
         cpu, _, _ = oracle_rate(w, float(os.environ.get("FCC_CPU_BASELINE_SECONDS", "12")),
                                 lambda n: Xh[:n].numpy())
+        # the same oracle on one host thread, on a smaller sample
+        cpu1, _, _ = oracle_rate(w, 2.0, lambda n: Xh[:n].numpy(), threads=1)
+        cpu["single_thread"] = {"value": cpu1["value"], "sample": cpu1["sample"]}
         # DRAM bytes per launch from the committed ncu capture, valid only while
         # the kernel source is the one that was captured
         traffic = None
