@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -369,6 +370,7 @@ def run_fcc(args, rank, world, local):
         # the same oracle on one host thread, on a smaller sample
         cpu1, _, _ = oracle_rate(w, 2.0, lambda n: Xh[:n].numpy(), threads=1)
         cpu["single_thread"] = {"value": cpu1["value"], "sample": cpu1["sample"]}
+        cpu["host"] = {"machine": platform.machine(), "nproc": os.cpu_count()}
         # DRAM bytes per launch from the committed ncu capture, valid only while
         # the kernel source is the one that was captured
         traffic = None
