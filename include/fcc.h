@@ -41,7 +41,7 @@ extern "C" {
 typedef enum {
     FCC_OK = 0,
     FCC_ERR_INVALID_ARG = 1,   /* a null/misaligned pointer or an out-of-range size */
-    FCC_ERR_UNSUPPORTED = 2,   /* valid request this build does not handle (e.g. M > 16) */
+    FCC_ERR_UNSUPPORTED = 2,   /* valid request the library does not handle (e.g. M > 16) */
     FCC_ERR_OOM = 3,           /* a device or pinned-host allocation failed */
     FCC_ERR_CUDA = 4,          /* a CUDA runtime / cuFFT call failed (see fcc_last_error) */
     FCC_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
