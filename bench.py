@@ -144,7 +144,7 @@ def oracle_rate(w, budget_s: float, X_sample_fn, threads=None):
     """Time the FP64 oracle (as it stands) on a sample sized to ~budget_s."""
     from oracle import oracle as O
     basis = O.Basis(w.N, w.L, w.lag_den)
-    nt = O.max_threads() if threads is None else threads
+    nt = len(os.sched_getaffinity(0)) if threads is None else threads
     X = X_sample_fn(64)
     t0 = time.perf_counter()
     O.tdoa(X, basis.WK, basis.taus, basis.delta, threads=nt)
@@ -176,16 +176,19 @@ def run_reference(args, rank, world):
         if n not in sample:
             sample[n] = w.spectra(T=n, seed=rank_seed(0)).numpy()
         return sample[n]
-    info, n, _ = oracle_rate(w, budget / 2, gen)
+    # every host core this process may use (a launcher's OMP_NUM_THREADS = 1 would
+    # otherwise leave the oracle on one thread)
+    nt = len(os.sched_getaffinity(0))
+    info, n, _ = oracle_rate(w, budget / 2, gen, threads=nt)
     from oracle import oracle as O
     basis = O.Basis(w.N, w.L, w.lag_den)
     X = gen(n)
     for _ in range(args.warmup):
-        O.tdoa(X[: max(1, n // 8)], basis.WK, basis.taus, basis.delta)
+        O.tdoa(X[: max(1, n // 8)], basis.WK, basis.taus, basis.delta, threads=nt)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        O.tdoa(X, basis.WK, basis.taus, basis.delta)
+        O.tdoa(X, basis.WK, basis.taus, basis.delta, threads=nt)
         times.append(time.perf_counter() - t0)
     v = n * w.P * args.steps / sum(times)
     info["value"] = v
