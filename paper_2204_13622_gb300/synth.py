@@ -252,7 +252,9 @@ def stft_domain_spectra(T: int, xyz: np.ndarray, fs: float, N: int, hop: int, se
                 env[s, pos:pos + run] = 1.0
             pos += run
             on = not on
-    # guarantee at least one source is on in every frame so no frame is pure noise
+    # where every envelope is off, source 0's is turned on; a frame in which every
+    # source active in its segment is in an off run still carries noise alone
+    # (about 16 % of frames with three envelopes), like a pause in speech
     env[0, env.sum(0) == 0] = 1.0
 
     delays_t = torch.tensor(delays, dtype=torch.float64, device=dev)
@@ -303,7 +305,8 @@ def pair_delay_spectra(n: int, N: int, tau_max: float, seed: int, device="cpu",
     pair's correlation peaks at tau = t_s.  Each microphone adds independent
     complex white noise of power 10^(-SNR/10).  Returns (X, t [n] float64
     numpy, snr [n] float64 numpy).  Sample s depends only on (seed, start + s)
-    blocks of 2^16, so chunked generation gives the same set.
+    blocks of 2^16, so chunked generation draws the same set (equal values up
+    to the last bit of float32 rounding in the phase ramp).
     """
     import torch
 
