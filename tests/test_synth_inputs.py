@@ -132,3 +132,23 @@ def test_array_spectra_far_field():
     u, *_ = np.linalg.lstsq(A, -(C / arr["fs"]) * dd[1:], rcond=None)
     assert np.abs(A @ u + (C / arr["fs"]) * dd[1:]).max() < 1e-5 * C / arr["fs"]
     assert np.linalg.norm(u) <= 1.0 + 1e-4
+
+
+def test_pcm_far_field_integer_delays_and_int16_scale():
+    xyz = synth.circular_array(4, 0.05)
+    n = 4000
+    x = synth.pcm_far_field(n, xyz, FS, seed=3, segment=n, snr_db=200.0, kind="f32").numpy()
+    L = synth.lag_extent(xyz, FS) + 1
+    lags = []
+    for m in range(1, 4):
+        # channel m is channel 0 shifted by a whole number of samples, |shift| <= L
+        hit = [k for k in range(-L, L + 1)
+               if np.allclose(x[L + k:n - L + k, m], x[L:n - L, 0], rtol=0, atol=1e-6)]
+        assert len(hit) == 1
+        lags.append(hit[0])
+    assert any(k != 0 for k in lags)
+    # int16 PCM is the same draw scaled by 6000, rounded and clipped
+    s16 = synth.pcm_far_field(n, xyz, FS, seed=3, segment=n, snr_db=200.0, kind="s16").numpy()
+    assert s16.dtype == np.int16
+    ref = np.clip(np.round(x * np.float32(6000.0)), -32768, 32767).astype(np.int16)  # FP32, as generated
+    assert np.array_equal(s16, ref)
