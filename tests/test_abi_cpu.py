@@ -79,3 +79,18 @@ def test_debug_hooks_validate_arguments(lib):
     assert lib.fcc_debug_set(0, 5000) == 0
     assert lib.fcc_debug_set(0, 0) == 0           # back to the default bound
     assert lib.fcc_debug_set(2, 0) == 0
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    # a valid plan on a machine with no GPU fails with FCC_ERR_CUDA and leaves
+    # no handle: nothing in the library computes on the host instead
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2204_13622_gb300 import binding
+    d = binding.PlanDesc(4, None, 16000.0, 512, 343.0, 3.0, 4, 0, 0.999, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.fcc_plan_create(ctypes.byref(d), ctypes.byref(h)) == 4 and not h.value
+    with pytest.raises(binding.FccError) as e:
+        binding.Plan(4, 16000.0, 512, 4, tau_max=3, device=0)
+    assert e.value.status == 4
