@@ -94,3 +94,37 @@ def test_no_cpu_fallback_without_a_gpu(lib):
     with pytest.raises(binding.FccError) as e:
         binding.Plan(4, 16000.0, 512, 4, tau_max=3, device=0)
     assert e.value.status == 4
+
+
+def test_remaining_entry_points_reject_null_arguments(lib):
+    # every entry point not covered above answers FCC_ERR_INVALID_ARG (1) to a
+    # null handle or output before it touches a device; destroy(NULL) is a no-op
+    N = None
+    h = ctypes.c_void_p()
+    d = ctypes.c_double
+    calls = [
+        lambda: lib.fcc_plan_taus(N, N),
+        lambda: lib.fcc_plan_singular_values(N, N, N, N, N),
+        lambda: lib.fcc_plan_bases(N, N, N, N, N),
+        lambda: lib.fcc_tdoa_host(N, N, 0, N, N, N, N),
+        lambda: lib.fcc_gcc_tdoa(N, N, 0, N, N, N, N),
+        lambda: lib.fcc_plan_sync(N, N),
+        lambda: lib.fcc_plan_geometry(N, N),
+        lambda: lib.fcc_plan_autotune(N, N, 0, 1, N),
+        lambda: lib.fcc_smooth_workspace(N, 10, N),
+        lambda: lib.fcc_tdoa_smoothed(N, N, 0, d(0.5), N, N, 0, N, N, N, N, N),
+        lambda: lib.fcc_batch_create(N, N, 0, 0, 0, N, ctypes.byref(h)),
+        lambda: lib.fcc_batch_info(N, N),
+        lambda: lib.fcc_batch_array_info(N, 0, N),
+        lambda: lib.fcc_batch_bind(N, N, N, N, N, N),
+        lambda: lib.fcc_batch_run(N, N),
+        lambda: lib.fcc_batch_sync(N, N),
+        lambda: lib.fcc_mlp_create(16, 128, N, d(0.1), N, 0, N),
+        lambda: lib.fcc_mlp_get_state(N, N, N, N, N),
+        lambda: lib.fcc_mlp_sync(N, N),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == 1, i
+    assert not h.value
+    lib.fcc_batch_destroy(N)
+    lib.fcc_mlp_destroy(N)
