@@ -121,7 +121,13 @@ def test_remaining_entry_points_reject_null_arguments(lib):
         lambda: lib.fcc_batch_sync(N, N),
         lambda: lib.fcc_mlp_create(16, 128, N, d(0.1), N, 0, N),
         lambda: lib.fcc_mlp_get_state(N, N, N, N, N),
+        lambda: lib.fcc_mlp_set_state(N, N, N, N, 0),
+        lambda: lib.fcc_mlp_gradient(N, N, N, N, 10, N, N, N),
+        lambda: lib.fcc_mlp_train_step(N, N, N, N, 10, ctypes.c_float(0.1), N, N),
+        lambda: lib.fcc_mlp_infer(N, N, N, 10, ctypes.c_float(0.5), N, N, N, N),
+        lambda: lib.fcc_tdoa_learned(N, N, N, 10, ctypes.c_float(0.5), N, N, N, N, N, N, N),
         lambda: lib.fcc_mlp_sync(N, N),
+        lambda: lib.fcc_plan_bases_noalloc(N, N, N, N, N, N, N, N, N),
     ]
     for i, call in enumerate(calls):
         assert call() == 1, i
