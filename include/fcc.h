@@ -129,17 +129,19 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *desc, fcc_plan_t **out);
 /* Release a plan (NULL is ignored).  Waits for the plan's device work. */
 void fcc_plan_destroy(fcc_plan_t *plan);
 
-/* Copy the plan's sizes into *info. */
+/* Copy the plan's sizes into *info (host memory).  Errors: INVALID_ARG (NULL). */
 fcc_status_t fcc_plan_info(const fcc_plan_t *plan, fcc_plan_info_t *info);
 
-/* Copy the lag grid tau_0..tau_{I-1} (samples) into host taus[I]. */
+/* Copy the lag grid tau_0..tau_{I-1} (samples, Sec. 3) into host taus[I].
+ * Errors: INVALID_ARG (NULL). */
 fcc_status_t fcc_plan_taus(const fcc_plan_t *plan, double *taus);
 
 /*
  * Copy every singular value of the even block (min(I, Q+1) values) and of the
  * odd block (min(I, Q) values), each in descending order, into host arrays
  * s_even / s_odd (either may be NULL); their counts go to *n_even / *n_odd.
- * Together they are the singular values of W (Sec. 4).
+ * Together they are the singular values of W (Sec. 4).  Errors: INVALID_ARG
+ * (NULL plan).
  */
 fcc_status_t fcc_plan_singular_values(const fcc_plan_t *plan, double *s_even, int *n_even,
                                       double *s_odd, int *n_odd);
@@ -156,6 +158,7 @@ fcc_status_t fcc_plan_singular_values(const fcc_plan_t *plan, double *s_even, in
  * For FCC_FORM_REIM_SPLIT plans: Pe[K_c][N/2+1] and Po[K_s][N/2+1] are the
  * cosine and sine projections (sigma_k v_k of C and S), Ue[I][K_c] and Uo[I][K_s]
  * their left vectors, and y = 2 (Ue (Pe Re x) - Uo (Po Im x)).
+ * Errors: INVALID_ARG (NULL plan).
  */
 fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, double *Ue, double *Uo);
 
@@ -187,6 +190,8 @@ fcc_status_t fcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int 
  * memory and the device error word has been checked.
  *   h_spectra complex64 [T][M][B]; h_lag_idx int32 [T][P]; h_peak float [T][P];
  *   h_tau_hat float [T][P] or NULL.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM (staging; nothing of it is kept),
+ * CUDA, NONFINITE, TIMEOUT.
  */
 fcc_status_t fcc_tdoa_host(fcc_plan_t *plan, const void *h_spectra, long long T,
                            int *h_lag_idx, float *h_peak, float *h_tau_hat, void *stream);
@@ -243,6 +248,7 @@ fcc_status_t fcc_plan_bases_noalloc(const fcc_plan_desc_t *desc, fcc_plan_info_t
 /*
  * Synchronise `stream` (NULL = legacy default), then read and clear the plan's
  * device error word: FCC_OK, FCC_ERR_NONFINITE or FCC_ERR_TIMEOUT.
+ * Errors: INVALID_ARG (NULL plan), CUDA.
  */
 fcc_status_t fcc_plan_sync(fcc_plan_t *plan, void *stream);
 

@@ -57,9 +57,11 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
 /* Synchronise the device and free the batch, its plans and its graph. */
 void fcc_batch_destroy(fcc_batch_t *batch);
 
+/* The batch's totals and classes into *info.  Errors: INVALID_ARG (NULL). */
 fcc_status_t fcc_batch_info(const fcc_batch_t *batch, fcc_batch_info_t *info);
 
-/* Sizes of array a's plan (P, I, K, ... as fcc_plan_info). */
+/* Sizes of array a's plan (P, I, K, ... as fcc_plan_info).
+ * Errors: INVALID_ARG (NULL, a out of range). */
 fcc_status_t fcc_batch_array_info(const fcc_batch_t *batch, int a, fcc_plan_info_t *info);
 
 /*
@@ -76,7 +78,7 @@ fcc_status_t fcc_batch_bind(fcc_batch_t *batch, const void *const *d_spectra, in
 fcc_status_t fcc_batch_run(fcc_batch_t *batch, void *stream);
 
 /* Synchronise `stream`, then read and clear the batch's device error word
- * (FCC_OK, FCC_ERR_NONFINITE or FCC_ERR_TIMEOUT). */
+ * (FCC_OK, FCC_ERR_NONFINITE or FCC_ERR_TIMEOUT).  Errors: INVALID_ARG (NULL), CUDA. */
 fcc_status_t fcc_batch_sync(fcc_batch_t *batch, void *stream);
 
 #ifdef __cplusplus

@@ -54,7 +54,8 @@ fcc_status_t fcc_doa_search(fcc_doa_t *doa, const float *d_corr, long long T, in
                             void *stream);
 
 /* Bytes of device workspace fcc_tdoa_doa needs (independent of T beyond a
- * chunk of frames whose correlations stay in L2). */
+ * chunk of frames whose correlations stay in L2).  Errors: INVALID_ARG (null,
+ * T < 0). */
 fcc_status_t fcc_doa_workspace(const fcc_doa_t *doa, long long T, long long *bytes);
 
 /*

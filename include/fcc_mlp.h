@@ -116,7 +116,8 @@ fcc_status_t fcc_tdoa_learned(fcc_plan_t *plan, fcc_mlp_t *mlp, const void *d_sp
                               float *d_coeffs, float *d_tau, float *d_conf, void *stream);
 
 /* Synchronise `stream`, then read and clear the head's device error word
- * (FCC_OK or FCC_ERR_TIMEOUT from a bounded wait of the inference kernel). */
+ * (FCC_OK or FCC_ERR_TIMEOUT from a bounded wait of the inference kernel).
+ * Errors: INVALID_ARG (NULL), CUDA. */
 fcc_status_t fcc_mlp_sync(fcc_mlp_t *mlp, void *stream);
 
 #ifdef __cplusplus

@@ -40,7 +40,8 @@ fcc_status_t fcc_stft(fcc_plan_t *plan, const void *d_pcm, fcc_pcm_t type, long 
 
 /* Bytes of device workspace recommended for fcc_tdoa_pcm: one chunk of spectra.
  * fcc_tdoa_pcm accepts any workspace of at least one frame of spectra (M (N/2+1)
- * 8 bytes) and processes the frames in chunks of as many as it holds. */
+ * 8 bytes) and processes the frames in chunks of as many as it holds.
+ * Errors: INVALID_ARG (null, n_samples < 0, hop < 1). */
 fcc_status_t fcc_pcm_workspace(const fcc_plan_t *plan, long long n_samples, int hop, long long *bytes);
 
 /*

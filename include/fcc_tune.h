@@ -31,7 +31,8 @@ typedef struct {
     long long smem_bytes;
 } fcc_geometry_t;
 
-/* The plan's current FP32 geometry (all zero when N > 1024: no FP32 kernel). */
+/* The plan's current FP32 geometry (all zero when N > 1024: no FP32 kernel).
+ * Errors: INVALID_ARG (NULL). */
 fcc_status_t fcc_plan_geometry(const fcc_plan_t *plan, fcc_geometry_t *out);
 
 /*
