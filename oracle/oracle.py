@@ -5,8 +5,10 @@ reference leg may import this module.  The product package never imports it and
 shares no code with it.
 
 This is a thin numpy/ctypes shell over ``fcc_oracle.c`` (compiled on first use
-with the system C compiler).  Every numeric step lives in the C file, which
-follows the paper's definitions literally in FP64:
+with the system C compiler).  Every numeric step lives in the C file, except
+the STFT, where numpy's rfft serves as the DFT of each windowed frame (a
+library primitive used as one step); the C file follows the paper's
+definitions literally in FP64:
 
 * Sec. 3 -- candidate grid tau_i = -L + i/r  (I = 2rL + 1).
 * Eq. 3 -- W(i, f) = exp(j 2 pi f tau_i / N), f = 0..N/2.
