@@ -1,6 +1,6 @@
 """Pins for the FP64 oracle of the learned TDoA head (an extension, not in the
 paper): the analytic gradient against central differences, closed forms of the
-forward pass and of Adam's first step, and bfloat16 rounding."""
+forward pass and of Adam's steps, and bfloat16 rounding."""
 import math
 
 import numpy as np
@@ -77,3 +77,23 @@ def test_round_bf16(O):
     assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125
     assert r[3] == 3.140625
     assert np.all(np.abs(r - vals) <= np.abs(vals) * 2.0 ** -8)
+
+
+def test_adam_constant_gradient_moves_signed_lr_every_step(O):
+    # With a constant gradient g the moments are m_t = (1 - b1^t) g and
+    # v_t = (1 - b2^t) g^2, so the bias-corrected ratio is exactly g / |g| and
+    # every step (eps = 0) moves each parameter by lr * sign(g).  An Adam that
+    # forgets its moments between steps, or corrects the bias with the wrong
+    # power of beta, moves by a different amount from step 2 on.
+    g = np.array([0.3, -4.0, 1e-3, -7e-5])
+    p0 = np.array([1.0, -2.0, 0.5, 3.0])
+    p = p0.copy()
+    m, v = np.zeros(4), np.zeros(4)
+    lr = 0.01
+    for step in range(1, 11):
+        before = p.copy()
+        O.adam(p, g, m, v, step, lr, eps=0.0)
+        assert np.allclose(before - p, lr * np.sign(g), rtol=0, atol=1e-14), step
+        assert np.allclose(m, (1 - 0.9 ** step) * g, rtol=1e-13, atol=0), step
+        assert np.allclose(v, (1 - 0.999 ** step) * g * g, rtol=1e-13, atol=0), step
+    assert np.allclose(p, p0 - 10 * lr * np.sign(g), rtol=0, atol=1e-13)
