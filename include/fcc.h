@@ -55,6 +55,25 @@ typedef enum {
     FCC_PREC_FP16 = 2   /* projection operands in FP16, FP32 accumulation (tensor cores) */
 } fcc_prec_t;
 
+/*
+ * Which kernel a plan runs fcc_tdoa on.  AUTO picks the tensor-memory kernel
+ * where it applies (N in [128, 1024], an even number of mics, folded form),
+ * else the CUDA-core kernel for FP32 plans and the shared-memory tensor-core
+ * kernel for BF16 / FP16 plans.
+ *   CUDA_CORES   the Eq. 9 projection in packed FP32 FMAs (FP32 plans only).
+ *   TENSOR_TMEM  the Eq. 9 projection as tcgen05 MMAs whose A operand (the
+ *                cross spectra) is written straight into tensor memory; FP32
+ *                plans use TF32 with a two-term split of both operands, BF16 /
+ *                FP16 plans one rounding of the cross spectra.
+ *   TENSOR_SMEM  the 16-bit forms with the A operand staged in shared memory.
+ */
+typedef enum {
+    FCC_ENGINE_AUTO = 0,
+    FCC_ENGINE_CUDA_CORES = 1,
+    FCC_ENGINE_TENSOR_TMEM = 2,
+    FCC_ENGINE_TENSOR_SMEM = 3
+} fcc_engine_t;
+
 typedef enum {
     FCC_FORM_FOLDED = 0,     /* the paper's even/odd bases on the folded x_s, x_d (Eqs. 6-9) */
     FCC_FORM_REIM_SPLIT = 1  /* cosine bases on Re x and sine bases on Im x: C = Re W and
@@ -131,6 +150,18 @@ void fcc_plan_destroy(fcc_plan_t *plan);
 
 /* Copy the plan's sizes into *info (host memory).  Errors: INVALID_ARG (NULL). */
 fcc_status_t fcc_plan_info(const fcc_plan_t *plan, fcc_plan_info_t *info);
+
+/*
+ * Select the kernel fcc_tdoa (and fcc_tdoa_host) runs for this plan (an
+ * fcc_engine_t; the same arithmetic of Secs. 2-4 on different hardware units).
+ * Not thread-safe against a concurrent launch on the same plan.
+ * Errors: INVALID_ARG (null plan, unknown engine), UNSUPPORTED (the engine does
+ * not apply to this plan's size or precision; the plan keeps its engine).
+ */
+fcc_status_t fcc_plan_set_engine(fcc_plan_t *plan, int engine);
+
+/* The engine fcc_tdoa runs for this plan (AUTO resolved).  Errors: INVALID_ARG (NULL). */
+fcc_status_t fcc_plan_get_engine(const fcc_plan_t *plan, int *engine);
 
 /* Copy the lag grid tau_0..tau_{I-1} (samples, Sec. 3) into host taus[I].
  * Errors: INVALID_ARG (NULL). */
@@ -228,8 +259,11 @@ fcc_status_t fcc_gcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, 
  * grids return FCC_ERR_UNSUPPORTED with the sizes in fcc_last_error().  No
  * other allocation is made on the device.
  *
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call uses the same array, so
+ * The first call on a device looks up the array's device address.  Under lazy
+ * module loading (the CUDA default) that first call may also be what loads the
+ * library's device code on that device, and the 4 MiB array is allocated when
+ * the code is loaded: make the first call before any stream capture and before
+ * the point from which the caller may no longer allocate.  Every call uses the same array, so
  * calls whose work overlaps on the GPU (from several threads or streams) race
  * and must be serialised by the caller.  Kernels and copies run on `stream`;
  * the call returns after synchronising it.

@@ -20,11 +20,13 @@ STATUS = {0: "FCC_OK", 1: "FCC_ERR_INVALID_ARG", 2: "FCC_ERR_UNSUPPORTED", 3: "F
           4: "FCC_ERR_CUDA", 5: "FCC_ERR_TIMEOUT", 6: "FCC_ERR_NONFINITE", 7: "FCC_ERR_NOT_CONVERGED"}
 PREC = {"fp32": 0, "bf16": 1, "fp16": 2}
 FORM = {"folded": 0, "reim": 1}
+ENGINE = {"auto": 0, "cuda_cores": 1, "tensor_tmem": 2, "tensor_smem": 3}
 
 # every symbol include/fcc.h declares
 EXPORTS = ["fcc_plan_create", "fcc_plan_destroy", "fcc_plan_info", "fcc_plan_taus",
            "fcc_plan_singular_values", "fcc_plan_bases", "fcc_tdoa", "fcc_tdoa_host", "fcc_gcc_tdoa",
            "fcc_plan_sync", "fcc_status_string", "fcc_last_error", "fcc_plan_bases_noalloc",
+           "fcc_plan_set_engine", "fcc_plan_get_engine",
            # include/fcc_mlp.h
            "fcc_mlp_num_params", "fcc_mlp_create", "fcc_mlp_destroy", "fcc_mlp_get_state",
            "fcc_mlp_set_state", "fcc_mlp_gradient", "fcc_mlp_train_step", "fcc_mlp_infer", "fcc_mlp_sync", "fcc_tdoa_learned",
@@ -111,6 +113,8 @@ def lib():
         L.fcc_tdoa_host.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
         L.fcc_gcc_tdoa.argtypes = [_vp, _vp, ctypes.c_longlong, _vp, _vp, _vp, _vp]
         L.fcc_plan_sync.argtypes = [_vp, _vp]
+        L.fcc_plan_set_engine.argtypes = [_vp, ctypes.c_int]
+        L.fcc_plan_get_engine.argtypes = [_vp, _ip]
         L.fcc_plan_bases_noalloc.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(PlanInfo), _dp, _dp,
                                              _dp, _dp, _dp, _dp, _vp]
         L.fcc_status_string.argtypes = [ctypes.c_int]
@@ -203,7 +207,7 @@ class Plan:
 
     def __init__(self, n_mics: int, fs: float, N: int, lag_den: int, tau_max: float = 0.0,
                  mic_xyz=None, c: float = 343.0, K: int = 0, energy: float = 0.999,
-                 prec: str = "fp32", device: int | None = None, form: str = "folded"):
+                 prec: str = "fp32", device: int | None = None, form: str = "folded", engine: str = "auto"):
         import torch
         if device is None:
             device = torch.cuda.current_device()
@@ -220,6 +224,18 @@ class Plan:
         info = PlanInfo()
         check(lib().fcc_plan_info(h, ctypes.byref(info)), "fcc_plan_info")
         self.info = {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+        if engine != "auto":
+            self.set_engine(engine)
+
+    def set_engine(self, engine: str):
+        """fcc_plan_set_engine: the kernel fcc_tdoa runs (see ENGINE)."""
+        check(lib().fcc_plan_set_engine(self._h, ENGINE[engine]), "fcc_plan_set_engine")
+
+    @property
+    def engine(self) -> str:
+        e = ctypes.c_int()
+        check(lib().fcc_plan_get_engine(self._h, ctypes.byref(e)), "fcc_plan_get_engine")
+        return {v: k for k, v in ENGINE.items()}[e.value]
 
     def __getattr__(self, name):
         info = self.__dict__.get("info")

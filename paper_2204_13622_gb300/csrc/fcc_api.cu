@@ -221,6 +221,7 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_err);
     cudaFree(p->d_tc_bases);
     cudaFree(p->d_tc_peq);
+    cudaFree(p->d_tm_btab);
     cudaFree(p->d_smooth_basis);
     cudaFree(p->d_stft_tab);
     pcm_destroy(p);
@@ -291,6 +292,18 @@ fcc_status_t fcc::plan_info_from_desc(const fcc_plan_desc_t *d, fcc_plan_info_t 
 }
 
 using namespace fcc;
+
+int fcc::resolved_engine(const fcc_plan *plan)
+{
+    switch (plan->engine) {
+    case FCC_ENGINE_CUDA_CORES: return FCC_ENGINE_CUDA_CORES;
+    case FCC_ENGINE_TENSOR_TMEM: return FCC_ENGINE_TENSOR_TMEM;
+    case FCC_ENGINE_TENSOR_SMEM: return FCC_ENGINE_TENSOR_SMEM;
+    default:
+        if (plan->info.prec == FCC_PREC_FP32) return FCC_ENGINE_CUDA_CORES;
+        return FCC_ENGINE_TENSOR_SMEM;
+    }
+}
 
 extern "C" {
 
@@ -408,6 +421,15 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
             return st;
         }
     }
+    if (in.form == FCC_FORM_FOLDED) {
+        // the tensor-memory path where it applies; a plan it does not apply to
+        // keeps the other engines (the reason stays in fcc_last_error)
+        st = prepare_tm(p);
+        if (st == FCC_ERR_OOM || st == FCC_ERR_CUDA) {
+            free_plan(p);
+            return st;
+        }
+    }
     if (debug_enabled())
         fprintf(stderr, "[fcc] plan M=%d N=%d I=%d K=%d (%d+%d) kh=%d slots=%d fp32: C=%d SB=%d GW=%d G=%d F=%d S=%d smem=%zu\n",
                 in.M, in.N, in.I, in.K, in.K_even, in.K_odd, p->kh, p->n_slots, p->geo.C, p->geo.SB, p->geo.GW,
@@ -422,6 +444,28 @@ void fcc_plan_destroy(fcc_plan_t *plan)
     DeviceScope scope(plan->device);
     cudaDeviceSynchronize();
     free_plan(plan);
+}
+
+fcc_status_t fcc_plan_set_engine(fcc_plan_t *plan, int engine)
+{
+    if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
+    if (engine < FCC_ENGINE_AUTO || engine > FCC_ENGINE_TENSOR_SMEM) return fail(FCC_ERR_INVALID_ARG, "engine");
+    const bool fp32 = plan->info.prec == FCC_PREC_FP32;
+    if (engine == FCC_ENGINE_CUDA_CORES && (!fp32 || plan->geo.G == 0))
+        return fail(FCC_ERR_UNSUPPORTED, "the CUDA-core kernel runs FP32 plans with N <= 1024");
+    if (engine == FCC_ENGINE_TENSOR_TMEM && !plan->tm.smem)
+        return fail(FCC_ERR_UNSUPPORTED, "the tensor-memory kernel does not apply to this plan");
+    if (engine == FCC_ENGINE_TENSOR_SMEM && (fp32 || !plan->tc_smem))
+        return fail(FCC_ERR_UNSUPPORTED, "the shared-memory tensor-core kernel runs BF16 / FP16 plans");
+    plan->engine = engine;
+    return FCC_OK;
+}
+
+fcc_status_t fcc_plan_get_engine(const fcc_plan_t *plan, int *engine)
+{
+    if (!plan || !engine) return fail(FCC_ERR_INVALID_ARG, "null plan or engine");
+    *engine = resolved_engine(plan);
+    return FCC_OK;
 }
 
 fcc_status_t fcc_plan_info(const fcc_plan_t *plan, fcc_plan_info_t *info)

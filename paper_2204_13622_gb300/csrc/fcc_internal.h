@@ -152,6 +152,40 @@ struct TcParams {
     unsigned *err;
 };
 
+// Geometry of the tensor-memory path (fcc_tmem.cu), chosen on the host per plan.
+struct TmGeometry {
+    int F = 0;    // frames per tile (F * slots <= 32: 128 TMEM lanes)
+    int S = 0;    // raw frame stages
+    int NI = 0;   // MMA-issuing warps (each with its own copy of D)
+    int NBA = 0;  // A buffers in the tensor-memory ring
+    int CH = 0;   // record quads per A buffer (chunk)
+    size_t smem = 0;
+};
+
+// Kernel parameters of the tensor-memory path (passed by value).
+struct TmParams {
+    const float2 *spectra;  // [T][M][B]
+    long long T;
+    int M, B, Q, P, n_slots, F, S, n_tiles;
+    int center, I, KE, KO, kh;
+    int nq;                 // record quads: Q / 4 + 1 (records 0..Q, then zeros)
+    int bq;                 // bytes of one quad's B block
+    int us;                 // bytes per unit-phase row (a multiple of 128)
+    int NI, NBA, CH;
+    float delta;
+    const void *btab;       // [nq][bq] B blocks (K-major core matrices)
+    const float *recon;     // as in Fp32Params
+    const Slot *slots;
+    int *out_idx;
+    float *out_peak;
+    float *out_tau;
+    float *out_coef;
+    float *out_corr;
+    unsigned *err;
+    long long wait_cycles;
+    int inject;             // test hook: CTA 0 withholds the copy of its first tile
+};
+
 }  // namespace fcc
 
 // The plan object behind the opaque ABI handle.
@@ -188,6 +222,10 @@ struct fcc_plan {
     float *d_tc_peq = nullptr;
     int tc_F = 0;
     size_t tc_smem = 0;
+    // tensor-memory path (fcc_tmem.cu)
+    void *d_tm_btab = nullptr;
+    fcc::TmGeometry tm{};
+    int engine = 0;                    // fcc_engine_t requested (FCC_ENGINE_AUTO = 0)
 };
 
 namespace fcc {
@@ -214,12 +252,21 @@ fcc_status_t launch_tc(const fcc_plan *plan, const float2 *spectra, long long T,
 // smoothing), and the split-form FP32 kernel's launch (alpha = 1).
 fcc_status_t prepare_reim(fcc_plan *plan);
 fcc_status_t launch_fp32_reim(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid);
-// FP32 (folded or split form) or tensor-core path, by the plan's precision.
+fcc_status_t prepare_tm(fcc_plan *plan);
+fcc_status_t launch_tm(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
+                       float *tau, float *coef, float *corr, cudaStream_t st);
+// The engine a plan runs fcc_tdoa on (fcc_engine_t, never AUTO).
+int resolved_engine(const fcc_plan *plan);
+// By the plan's engine: the CUDA-core kernel (FP32, folded or split form), the
+// tensor-memory kernel, or the shared-memory tensor-core kernel (16-bit forms).
 inline fcc_status_t launch_tdoa(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                                 float *tau, float *coef, float *corr, cudaStream_t st)
 {
-    return plan->info.prec == FCC_PREC_FP32 ? launch_fp32(plan, spectra, T, idx, peak, tau, coef, corr, st)
-                                            : launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
+    switch (resolved_engine(plan)) {
+    case FCC_ENGINE_TENSOR_TMEM: return launch_tm(plan, spectra, T, idx, peak, tau, coef, corr, st);
+    case FCC_ENGINE_TENSOR_SMEM: return launch_tc(plan, spectra, T, idx, peak, tau, coef, corr, st);
+    default: return launch_fp32(plan, spectra, T, idx, peak, tau, coef, corr, st);
+    }
 }
 void pcm_destroy(fcc_plan *plan);
 // Plan-time tables of the per-pair kernel (folded form) and of the STFT front-end.
