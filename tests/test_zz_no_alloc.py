@@ -70,3 +70,19 @@ def test_noalloc_rejects_grids_beyond_the_static_array(B):
                                        None, None, None)
     assert st == 2  # FCC_ERR_UNSUPPORTED
     assert "static array" in B.lib().fcc_last_error().decode()
+
+
+def test_noalloc_calls_leave_device_memory_unchanged(B):
+    # the first call on the device may load the library's device code, which
+    # allocates the static array; after it, calls must not change the amount of
+    # free device memory (no cudaMalloc, no library workspace, no torch tensor)
+    B.plan_bases_noalloc(2, 16000.0, 512, 4, tau_max=5)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for N, L, den in [(512, 5, 4), (1024, 12, 8), (256, 3, 4), (512, 5, 4)]:
+        B.plan_bases_noalloc(2, 16000.0, N, den, tau_max=L)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, f"free device memory changed by {free0 - free1} bytes"
+    assert torch.cuda.memory_allocated() == torch_bytes0
