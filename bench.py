@@ -213,7 +213,9 @@ def accuracy_vs_oracle(w, plan, X, out, n=1 << 14):
     n = min(n, T)
     frames = torch.from_numpy(np.linspace(0, T - 1, n).astype(np.int64)).to(X.device)
     Xs = X[frames].cpu().numpy()
-    ref = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+    ref = O.Basis(w.N, w.L, w.lag_den)  # K from the oracle's own energy rule
+    if ref.K != plan.K:
+        raise RuntimeError(f"plan K {plan.K} differs from the oracle's K {ref.K}")
     idx, peak, _, y = O.tdoa(Xs, ref.WK, ref.taus, ref.delta, want_y=True)
     gi = out["lag_idx"][frames].cpu().numpy()
     gp = out["peak"][frames].cpu().numpy()
@@ -242,7 +244,9 @@ def accuracy_time_domain(w, plan, n_frames=1 << 14, seed=7):
     X = torch.from_numpy(np.ascontiguousarray(rec.spectra)).to(torch.device("cuda", plan.device))
     out = plan.tdoa(X)
     plan.sync()
-    ref = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+    ref = O.Basis(w.N, w.L, w.lag_den)
+    if ref.K != plan.K:
+        raise RuntimeError(f"plan K {plan.K} differs from the oracle's K {ref.K}")
     idx, _, _, y = O.tdoa(rec.spectra, ref.WK, ref.taus, ref.delta, want_y=True)
     gi = out["lag_idx"].cpu().numpy()
     srt = np.sort(y, -1)
@@ -267,7 +271,7 @@ def run_fcc(args, rank, world, local):
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
     X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
-    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, prec=args.prec)
+    plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, prec=args.prec, engine=args.engine)
     out = plan.tdoa(X, tau_hat=True)  # allocates the outputs once
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 3)):
@@ -307,6 +311,7 @@ def run_fcc(args, rank, world, local):
             res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                    "warmup": args.warmup, "ms_per_step": ms_max, "config": {"workload": w.name, "frames": T},
                    "note": "FCC kernel only (profiling run)", "roofline_achieved_gbs": achieved,
+                   "engine": plan.engine,
                    "dtype": args.prec, "roofline_frac": achieved / float(json.load(open(os.path.join(
                        ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) if os.path.exists(os.path.join(
                            ROOT, "MEASURED_PEAKS.json")) else None, "accuracy_vs_oracle": acc,
@@ -495,6 +500,85 @@ def _peak_hbm():
     if os.path.exists(f):
         return float(json.load(open(f)).get("hbm_gbs", 6800.0)), "measured (MEASURED_PEAKS.json hbm_gbs)"
     return 6800.0, "fallback"
+
+
+def run_precision(args, local, steps):
+    """The 16-microphone grid (2^18 frames, N = 1024, I = 193, K = 15) in the three
+    precisions: FP32 (CUDA-core projection), BF16 and FP16 (tcgen05 projection,
+    FP32 accumulation).  Per precision: device time per pass, pair-frames/s, the
+    HBM roofline of its kernel, and agreement with the FP64 oracle on 2^14
+    frames spread over the workload (the oracle runs once; every precision is
+    compared with the same values)."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    from paper_2204_13622_gb300 import binding, workloads
+    w = workloads.GRID16
+    dev = torch.device("cuda", local)
+    T, P = w.T, w.P
+    X = w.spectra(T=T, device=dev, seed=rank_seed(0) + 1)
+    n = min(1 << 14, T)
+    frames = torch.from_numpy(np.linspace(0, T - 1, n).astype(np.int64)).to(dev)
+    Xs = X[frames].cpu().numpy()
+    ref = O.Basis(w.N, w.L, w.lag_den)
+    t0 = time.perf_counter()
+    idx, peak, _, y = O.tdoa(Xs, ref.WK, ref.taus, ref.delta, want_y=True)
+    t_or = time.perf_counter() - t0
+    scale = np.abs(y).max(-1)
+    srt = np.sort(y, -1)
+    clear = (srt[..., -1] - srt[..., -2]) / scale > 4e-6
+    del y, srt
+    peak_hbm, psrc = _peak_hbm()
+    bytes_per_launch = T * (w.M * w.B * 8) + T * P * 12
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": w.name, "frames": T, "mics": w.M, "pairs": P, "N": w.N,
+           "lag_grid": f"[-{w.L}, {w.L}] step 1/{w.lag_den}", "K": ref.K, "steps": steps,
+           "oracle_sample": f"{n} frames spread over the workload ({n * P} pair-frames), FP64 C oracle "
+                            f"({t_or:.1f} s on {O.max_threads()} host threads)",
+           "l2": f"inputs ({X.numel() * 8 / 1e9:.1f} GB) larger than L2; no flush"}
+    for prec in ("fp32", "bf16", "fp16"):
+        plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, prec=prec)
+        if plan.K != ref.K:
+            raise RuntimeError(f"{prec} plan K {plan.K} differs from the oracle's K {ref.K}")
+        out = plan.tdoa(X, tau_hat=True)
+        for _ in range(3):
+            plan.tdoa(X, out=out)
+        plan.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            ev[0].record(stream)
+            for k in range(steps):
+                plan.tdoa(X, out=out)
+                ev[k + 1].record(stream)
+            torch.cuda.synchronize(dev)
+        plan.sync()
+        per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+        ms = sum(per) / steps
+        gi = out["lag_idx"][frames].cpu().numpy()
+        gp = out["peak"][frames].cpu().numpy()
+        achieved = bytes_per_launch / (ms / 1000.0) / 1e9
+        res[prec] = {"ms_per_step": ms, "value": T * P / (ms / 1000.0), "unit": UNIT,
+                     "step_ms": [round(x, 3) for x in per], "gpu_launches": steps,
+                     "kernel": "fcc_fp32_kernel" if prec == "fp32" else "fcc_tc_kernel",
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                                  "frac": achieved / peak_hbm, "bytes_per_launch": bytes_per_launch,
+                                  "peak_source": psrc},
+                     "accuracy_vs_oracle": {
+                         "pair_frames": int(gi.size), "argmax_agreement": float((gi == idx).mean()),
+                         "argmax_agreement_clear": float((gi == idx)[clear].mean()),
+                         "peak_rel_err_median": float(np.median(np.abs(gp - peak) / scale)),
+                         "peak_rel_err_max": float(np.max(np.abs(gp - peak) / scale))},
+                     "clocks": clk.summary()}
+        if prec == "fp32":
+            res[prec]["roofline_alu"] = alu_roofline(
+                fp32_ops_per_pair_frame(w.M, w.N, plan.K_even, plan.K_odd, plan.I) * T * P, ms, "fcc_fp32_kernel")
+        del out
+        plan.close()
+    del X
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_batched(args, rank, world, local):
@@ -1095,6 +1179,33 @@ def run_learned(args, rank, world, local):
     return res
 
 
+def run_extras(args, local):
+    """The default line's other workloads, each at its full size: the 16-mic
+    grid in FP32 / BF16 / FP16 ("precision"), 4096 mixed arrays in one step
+    ("batched") and the learned head ("learned").  Each leg frees its device
+    memory before the next one starts."""
+    import copy
+
+    import torch
+    steps = max(3, min(args.steps, 5))
+    extras = {}
+    t0 = time.perf_counter()
+    extras["precision"] = run_precision(args, local, steps)
+    extras["precision"]["wall_s"] = round(time.perf_counter() - t0, 1)
+    torch.cuda.empty_cache()
+    a = copy.copy(args)
+    a.steps, a.warmup = steps, 3
+    t0 = time.perf_counter()
+    extras["batched"] = run_batched(a, 0, 1, local)
+    extras["batched"]["wall_s"] = round(time.perf_counter() - t0, 1)
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    extras["learned"] = run_learned(a, 0, 1, local)
+    extras["learned"]["wall_s"] = round(time.perf_counter() - t0, 1)
+    torch.cuda.empty_cache()
+    return extras
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1106,6 +1217,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="circle8",
                     choices=["circle8", "grid16", "square4", "batched", "learned", "doa", "pcm", "table1"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--engine", default="auto", choices=["auto", "cuda_cores", "tensor_tmem", "tensor_smem"],
+                    help="the kernel fcc_tdoa runs (fcc_plan_set_engine)")
     ap.add_argument("--alpha", type=float, default=1.0,
                     help="Eq. 1 smoothing factor; < 1 times the smoothed path (FCC leg only)")
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays")
@@ -1118,6 +1231,8 @@ def main(argv=None):
     ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")
     ap.add_argument("--heldout", type=int, default=1_000_000, help="learned: held-out pair-frames")
     ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="default line: skip the 16-mic precision, batched and learned-head legs")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -1141,6 +1256,9 @@ def main(argv=None):
             res = run_table1(args, rank, world, local) if rank == 0 else None
         else:
             res = run_fcc(args, rank, world, local)
+            if res is not None and args.extras and world == 1 and args.workload == "circle8" \
+                    and args.prec == "fp32" and args.only == "all" and not args.frames:
+                res.update(run_extras(args, local))
     if res is not None:
         print(json.dumps(res), flush=True)
 
