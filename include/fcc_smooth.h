@@ -34,14 +34,15 @@ fcc_status_t fcc_smooth_workspace(const fcc_plan_t *plan, long long T, long long
  * [P][N/2+1] (pairs i < j lexicographic, bins 0..N/2): R(0) on entry, R(T) on
  * return; NULL = a fresh stream whose final state is not kept.  d_work: device
  * workspace of at least fcc_smooth_workspace bytes.  Outputs as fcc_tdoa
- * (d_tau_hat and d_coeffs may be NULL).  Asynchronous on `stream`; the device
+ * (d_tau_hat, d_coeffs and d_corr may be NULL; d_corr receives y(tau_i) of
+ * every pair-frame, float [T][P][I]).  Asynchronous on `stream`; the device
  * error word (NaN / Inf input, a wait that ran out) is read by fcc_plan_sync.
  * Errors: INVALID_ARG (alpha outside (0, 1], pointers, workspace too small),
  * UNSUPPORTED, CUDA.
  */
 fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long long T, double alpha, void *d_state,
                                void *d_work, long long work_bytes, int *d_lag_idx, float *d_peak, float *d_tau_hat,
-                               float *d_coeffs, void *stream);
+                               float *d_coeffs, float *d_corr, void *stream);
 
 #ifdef __cplusplus
 }

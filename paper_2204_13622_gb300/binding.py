@@ -153,7 +153,7 @@ def lib():
         L.fcc_smooth_workspace.argtypes = [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
         L.fcc_smooth_workspace.restype = ctypes.c_int
         L.fcc_tdoa_smoothed.argtypes = [_vp, _vp, ctypes.c_longlong, ctypes.c_double, _vp, _vp, ctypes.c_longlong,
-                                        _vp, _vp, _vp, _vp, _vp]
+                                        _vp, _vp, _vp, _vp, _vp, _vp]
         L.fcc_tdoa_smoothed.restype = ctypes.c_int
         L.fcc_batch_sync.argtypes = [_vp, _vp]
         L.fcc_doa_create.argtypes = [_vp, _dp, _dp, ctypes.c_int, ctypes.POINTER(_vp)]
@@ -366,7 +366,7 @@ class Plan:
         return b.value
 
     def tdoa_smoothed(self, X, alpha: float, state=None, tau_hat: bool = True, coeffs: bool = False,
-                      work=None, stream=None, out=None):
+                      corr: bool = False, work=None, stream=None, out=None):
         """fcc_tdoa_smoothed: Eq. 1's recursive cross-spectrum with factor alpha,
         then FCC.  `state`: complex64 [P, B] device tensor holding R(0) on entry
         and R(T) on return (None: a fresh stream, final state dropped)."""
@@ -386,9 +386,12 @@ class Plan:
                 out["tau_hat"] = torch.empty((T, self.P), dtype=torch.float32, device=dev)
             if coeffs:
                 out["coeffs"] = torch.empty((T, self.P, 2 * self.K), dtype=torch.float32, device=dev)
+            if corr:
+                out["corr"] = torch.empty((T, self.P, self.I), dtype=torch.float32, device=dev)
         check(lib().fcc_tdoa_smoothed(self._h, _ptr(X), T, float(alpha), _ptr(state), _ptr(work), work.numel(),
                                       _ptr(out["lag_idx"]), _ptr(out["peak"]), _ptr(out.get("tau_hat")),
-                                      _ptr(out.get("coeffs")), _stream(stream, dev)), "fcc_tdoa_smoothed")
+                                      _ptr(out.get("coeffs")), _ptr(out.get("corr")), _stream(stream, dev)),
+              "fcc_tdoa_smoothed")
         return out
 
     # ---- STFT front-end (include/fcc_stft.h)

@@ -47,6 +47,7 @@ struct SmoothParams {
     float *out_peak;
     float *out_tau;
     float *out_coef;
+    float *out_corr;        // nullable, [T][P][I]
     unsigned *err;
     long long wait_cycles;
     int inject;             // test hook: CTA 0 withholds the copy of its first frame
@@ -400,12 +401,14 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
             float best = -FLT_MAX;
             int bi = 0x7fffffff;
             if (pq >= 0) {
+                float *corr = p.out_corr ? p.out_corr + ((size_t)(t0 + k) * p.P + pq) * p.I : nullptr;
                 float S, D;
                 int m = gi;
                 if (gi == 0) {
                     eval_SD<KH>(recon, 0, zE, zO, S, D);
                     best = S - D;
                     bi = p.center;
+                    if (corr) corr[p.center] = best;
                     m = 8;
                 }
                 for (; m <= p.center; m += 8) {
@@ -418,6 +421,10 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                     if (yp > best) {
                         best = yp;
                         bi = p.center + m;
+                    }
+                    if (corr) {
+                        corr[p.center - m] = ym;
+                        corr[p.center + m] = yp;
                     }
                 }
             }
@@ -585,7 +592,8 @@ namespace {
 // The per-pair kernel over T frames: `carry` (may be null: every chunk starts
 // from R = 0, which is exact for alpha = 1) holds the state entering each chunk.
 fcc_status_t run_per_pair(const fcc_plan *plan, const SmoothPlan &g, const float2 *spectra, long long T, float a,
-                          float b, const float2 *carry, int *idx, float *peak, float *tau, float *coef, cudaStream_t s)
+                          float b, const float2 *carry, int *idx, float *peak, float *tau, float *coef, float *corr,
+                          cudaStream_t s)
 {
     const fcc_plan_info_t &in = plan->info;
     SmoothParams prm{};
@@ -613,6 +621,7 @@ fcc_status_t run_per_pair(const fcc_plan *plan, const SmoothPlan &g, const float
     prm.out_peak = peak;
     prm.out_tau = tau;
     prm.out_coef = coef;
+    prm.out_corr = corr;
     prm.err = plan->d_err;
     DebugHooks &dh = debug_hooks();
     prm.wait_cycles = dh.wait_cycles;
@@ -674,7 +683,7 @@ fcc_status_t fcc_smooth_workspace(const fcc_plan_t *plan, long long T, long long
 
 fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long long T, double alpha, void *d_state,
                                void *d_work, long long work_bytes, int *d_lag_idx, float *d_peak, float *d_tau_hat,
-                               float *d_coeffs, void *stream)
+                               float *d_coeffs, float *d_corr, void *stream)
 {
     if (!plan) return fail(FCC_ERR_INVALID_ARG, "null plan");
     if (!(alpha > 0.0 && alpha <= 1.0)) return fail(FCC_ERR_INVALID_ARG, "alpha must be in (0, 1]");
@@ -715,7 +724,7 @@ fcc_status_t fcc_tdoa_smoothed(fcc_plan_t *plan, const void *d_spectra, long lon
     }
     if (!plan->d_smooth_basis) return fail(FCC_ERR_UNSUPPORTED, "the plan has no per-pair tables");
     return run_per_pair(plan, g, static_cast<const float2 *>(d_spectra), T, a, b, work, d_lag_idx, d_peak, d_tau_hat,
-                        d_coeffs, s);
+                        d_coeffs, d_corr, s);
 }
 
 }  // extern "C"

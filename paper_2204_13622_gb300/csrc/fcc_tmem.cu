@@ -41,9 +41,10 @@
 //     c % NI, which accumulates it into its own copy of D (one thread issues
 //     tcgen05.mma serially; several issuing warps overlap), so the sum is
 //     deterministic;
-//   * warps 12-15 epilogue, one per lane quadrant: tcgen05.ld of the NI copies
-//     of their lane (one pair-frame per thread), the reconstruction on the lag
-//     grid, argmax, refinement and outputs as the CUDA-core kernel.
+//   * warps 12-15 epilogue, one per lane quadrant, a tile behind the MMAs (two
+//     D buffers): tcgen05.ld of the NI copies of their lane (one pair-frame per
+//     thread), the reconstruction on the lag grid, argmax, refinement and
+//     outputs as the CUDA-core kernel.
 // Every wait is bounded; on expiry the kernel latches FCC_ERR_TIMEOUT, waits
 // (with the full bound) for its own copies and MMAs in flight, frees its tensor
 // memory and returns.
@@ -75,12 +76,12 @@ enum {
     kTbRawEmpty = 4,            // [kTmMaxStages]
     kTbAFull = 8,               // [kTmMaxA]
     kTbAEmpty = 16,             // [kTmMaxA]
-    kTbDFull = 24,
-    kTbDEmpty = 25,
-    kTbUFree = 26,
-    kTbUReady = 27,
-    kTbIssDone = 28,            // [kTmMaxIss]
-    kTbCount = 32
+    kTbDFull = 24,              // [2]: D buffer (tile parity) complete
+    kTbDEmpty = 26,             // [2]: D buffer read by the epilogue
+    kTbUFree = 28,
+    kTbUReady = 29,
+    kTbIssDone = 30,            // [kTmMaxIss]
+    kTbCount = 34
 };
 constexpr int kTmMaxStages = 4;
 constexpr int kTmMaxA = 8;
@@ -205,10 +206,34 @@ __device__ __forceinline__ void tm_ld16(uint32_t taddr, float *v)
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// mbarrier try_wait that may suspend the thread (up to hint_ns) until the
+// phase completes, so waiting warps take no issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity, unsigned hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase (false when `limit` cycles pass first).
+__device__ bool tm_wait(uint64_t *bar, unsigned parity, long long limit)
+{
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
 // A bounded wait whose outcome is the same in every lane of the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, unsigned parity, long long limit)
 {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit));
+    return __all_sync(0xffffffffu, tm_wait(bar, parity, limit));
 }
 
 template <int KH, int PREC>
@@ -246,8 +271,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
             mbar_init(&bar[kTbAFull + b], kTmProd);
             mbar_init(&bar[kTbAEmpty + b], 1);
         }
-        mbar_init(&bar[kTbDFull], (unsigned)p.NI);
-        mbar_init(&bar[kTbDEmpty], kTmEpi);
+        for (int d = 0; d < 2; ++d) {
+            mbar_init(&bar[kTbDFull + d], (unsigned)p.NI);
+            mbar_init(&bar[kTbDEmpty + d], kTmEpi);
+        }
         mbar_init(&bar[kTbUFree], kTmProd);
         mbar_init(&bar[kTbUReady], kTmProd);
         for (int i = 0; i < kTmMaxIss; ++i) mbar_init(&bar[kTbIssDone + i], 1);
@@ -272,7 +299,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t a0col = (uint32_t)(p.NI * DW);  // A ring starts after the D copies
+    const uint32_t a0col = (uint32_t)(2 * p.NI * DW);  // A ring after two buffers of NI copies of D
 
     auto tile_frames = [&](int j, int &nf) {
         const long long f0 = ((long long)blockIdx.x + (long long)j * gridDim.x) * p.F;
@@ -286,7 +313,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
             int issued = 0;
             for (int j = 0; j < n_local; ++j) {
                 const int s = j % p.S;
-                if (!mbar_wait(&bar[kTbRawEmpty + s], ((unsigned)(j / p.S) & 1u) ^ 1u, p.wait_cycles)) {
+                if (!tm_wait(&bar[kTbRawEmpty + s], ((unsigned)(j / p.S) & 1u) ^ 1u, p.wait_cycles)) {
                     atomicOr(p.err, kErrTimeout);
                     break;
                 }
@@ -303,7 +330,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
             // never retire with a copy in flight: wait (full bound) for the last copy of every stage
             for (int j = max(0, issued - p.S); j < issued; ++j) {
                 if (p.inject && blockIdx.x == 0 && j == 0) continue;
-                if (!mbar_wait(&bar[kTbRawFull + j % p.S], (unsigned)(j / p.S) & 1u, kWaitCycles))
+                if (!tm_wait(&bar[kTbRawFull + j % p.S], (unsigned)(j / p.S) & 1u, kWaitCycles))
                     atomicOr(p.err, kErrTimeout);
             }
         }
@@ -315,19 +342,20 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                                          : (PREC == FCC_PREC_BF16 ? ((1u << 7) | (1u << 10)) : 0u);
             constexpr uint32_t idesc = (1u << 4) | fmt | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             const uint32_t btab = smem_u32(smem + lay.btab);
-            const uint32_t d_re = tmem + (uint32_t)(iw * DW), d_im = d_re + 4 * KT;
             long long g = 0;
             bool ok = true, any = false;
             for (int j = 0; j < n_local && ok; ++j) {
                 bool first = true;
+                const int db = j & 1;  // D buffer of this tile: the epilogue runs a tile behind
+                const uint32_t d_re = tmem + (uint32_t)((db * p.NI + iw) * DW), d_im = d_re + 4 * KT;
                 for (int c = 0; c < n_ch; ++c, ++g) {
                     if (c % p.NI != iw) continue;
-                    if (first && !mbar_wait(&bar[kTbDEmpty], ((unsigned)j & 1u) ^ 1u, p.wait_cycles)) {
+                    if (first && !tm_wait(&bar[kTbDEmpty + db], ((unsigned)(j >> 1) & 1u) ^ 1u, p.wait_cycles)) {
                         ok = false;
                         break;
                     }
                     const int b = (int)(g % p.NBA);
-                    if (!mbar_wait(&bar[kTbAFull + b], (unsigned)(g / p.NBA) & 1u, p.wait_cycles)) {
+                    if (!tm_wait(&bar[kTbAFull + b], (unsigned)(g / p.NBA) & 1u, p.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -352,12 +380,12 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                     any = true;
                 }
                 if (!ok) break;
-                umma_commit(&bar[kTbDFull]);
+                umma_commit(&bar[kTbDFull + db]);
             }
             if (!ok) atomicOr(p.err, kErrTimeout);
             // retire only when every MMA this warp issued has completed
             umma_commit(&bar[kTbIssDone + iw]);
-            if (!mbar_wait(&bar[kTbIssDone + iw], 0u, kWaitCycles)) atomicOr(p.err, kErrTimeout);
+            if (!tm_wait(&bar[kTbIssDone + iw], 0u, kWaitCycles)) atomicOr(p.err, kErrTimeout);
             (void)any;
         }
     } else if (warp < kTmProd) {
@@ -422,17 +450,70 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                 ok = false;
                 break;
             }
-            // ---- this lane group's slot: four row pointers and their swizzles
+            // ---- this lane group's slot.  Record f = 4h + tt of a row sits at position
+            // f ^ sw = 4 (h ^ (sw / 4)) + tt; chunks hold an even number of quads, so
+            // the quads h of this warp all have the parity hh and each row's record
+            // address is a fixed base + 64 h.
             const bool act = sidx < TS && fl < nf;
-            const unsigned char *urow[4];
-            int sw[4];
+            const unsigned char *ub[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int mic = act ? sl.mic[r] : 0;
-                urow[r] = ubuf + (size_t)(fl * M + mic) * p.us;
-                sw[r] = tm_swz(mic);
+                const int s4 = tm_swz(mic) >> 2;
+                ub[r] = ubuf + (size_t)(fl * M + mic) * p.us + 16 * tt + (s4 ? (hh ? -64 : 64) : 0);
             }
-            // ---- A chunks
+            // cross spectra of one record for the slot's four pairs, packed over the two
+            // bins: re[q] = (Re a, Re b), im[q] = (Im a, Im b)
+            auto record = [&](int h, f2 (&re)[4], f2 (&im)[4]) {
+                float4 X[2], Y[2];
+                if (act) {
+                    X[0] = *reinterpret_cast<const float4 *>(ub[0] + 64 * h);
+                    X[1] = *reinterpret_cast<const float4 *>(ub[1] + 64 * h);
+                    Y[0] = *reinterpret_cast<const float4 *>(ub[2] + 64 * h);
+                    Y[1] = *reinterpret_cast<const float4 *>(ub[3] + 64 * h);
+                } else {
+                    X[0] = X[1] = Y[0] = Y[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                f2 xr[2], xi[2], nxr[2], yr[2], yi[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    xr[u] = pk(X[u].x, X[u].y);
+                    xi[u] = pk(X[u].z, X[u].w);
+                    nxr[u] = pk(-X[u].x, -X[u].y);
+                    yr[u] = pk(Y[u].x, Y[u].y);
+                    yi[u] = pk(Y[u].z, Y[u].w);
+                }
+                // pair (ix, iy): (Re a, Re b) = xr yr + xi yi, (Im a, Im b) = xi yr - xr yi
+#pragma unroll
+                for (int pq = 0; pq < 4; ++pq) {
+                    const int ix = pq >> 1, iy = pq & 1;
+                    re[pq] = fma2(xi[ix], yi[iy], mul2(xr[ix], yr[iy]));
+                    im[pq] = fma2(nxr[ix], yi[iy], mul2(xi[ix], yr[iy]));
+                }
+            };
+            auto store = [&](uint32_t col, const f2 (&re)[4], const f2 (&im)[4]) {
+#pragma unroll
+                for (int hb = 0; hb < 2; ++hb) {
+                    const uint32_t taddr = col + ((uint32_t)(32 * q + 16 * hb) << 16);
+                    const int p0 = 2 * hb, p1 = 2 * hb + 1;
+                    if constexpr (F32) {
+                        const f2 rl0 = tf32_lo(re[p0]), il0 = tf32_lo(im[p0]);
+                        const f2 rl1 = tf32_lo(re[p1]), il1 = tf32_lo(im[p1]);
+                        const uint32_t r[16] = {f2lo(re[p0]), f2hi(re[p0]), f2lo(re[p1]), f2hi(re[p1]),
+                                                f2lo(im[p0]), f2hi(im[p0]), f2lo(im[p1]), f2hi(im[p1]),
+                                                f2lo(rl0),    f2hi(rl0),    f2lo(rl1),    f2hi(rl1),
+                                                f2lo(il0),    f2hi(il0),    f2lo(il1),    f2hi(il1)};
+                        tm_st_x4(taddr, r);
+                    } else {
+                        tm_st_x1(taddr, tm_pack16<PREC>(re[p0]), tm_pack16<PREC>(im[p0]), tm_pack16<PREC>(re[p1]),
+                                 tm_pack16<PREC>(im[p1]));
+                    }
+                }
+            };
+            // ---- A chunks: the next record's loads and arithmetic run before the wait
+            // for the previous record's tensor-memory stores
+            f2 cre[4], cim[4];
+            record(hh, cre, cim);  // chunk 0, quad hh (every chunk holds at least two quads)
             for (int c = 0; c < n_ch; ++c, ++g) {
                 const int b = (int)(g % p.NBA);
                 if (!warp_wait(&bar[kTbAEmpty + b], ((unsigned)(g / p.NBA) & 1u) ^ 1u, p.wait_cycles)) {
@@ -441,50 +522,20 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                 }
                 const int nqc = min(p.CH, p.nq - c * p.CH);
                 for (int qq = hh; qq < nqc; qq += 2) {
-                    const int f = 4 * (c * p.CH + qq) + tt;  // this thread's record
-                    float4 X[2], Y[2];
-                    if (act) {
-                        X[0] = *reinterpret_cast<const float4 *>(urow[0] + 16 * (f ^ sw[0]));
-                        X[1] = *reinterpret_cast<const float4 *>(urow[1] + 16 * (f ^ sw[1]));
-                        Y[0] = *reinterpret_cast<const float4 *>(urow[2] + 16 * (f ^ sw[2]));
-                        Y[1] = *reinterpret_cast<const float4 *>(urow[3] + 16 * (f ^ sw[3]));
-                    } else {
-                        X[0] = X[1] = Y[0] = Y[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    // packed over the two bins of the record: (re f, re f'), (im f, im f')
-                    f2 xr[2], xi[2], nxr[2], yr[2], yi[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        xr[u] = pk(X[u].x, X[u].y);
-                        xi[u] = pk(X[u].z, X[u].w);
-                        nxr[u] = pk(-X[u].x, -X[u].y);
-                        yr[u] = pk(Y[u].x, Y[u].y);
-                        yi[u] = pk(Y[u].z, Y[u].w);
-                    }
-                    // pair (ix, iy): (Re a, Re b) = xr yr + xi yi, (Im a, Im b) = xi yr - xr yi
-                    f2 re[4], im[4];
-#pragma unroll
-                    for (int pq = 0; pq < 4; ++pq) {
-                        const int ix = pq >> 1, iy = pq & 1;
-                        re[pq] = fma2(xi[ix], yi[iy], mul2(xr[ix], yr[iy]));
-                        im[pq] = fma2(nxr[ix], yi[iy], mul2(xi[ix], yr[iy]));
-                    }
                     const uint32_t col = tmem + a0col + (uint32_t)((b * p.CH + qq) * CW);
+                    f2 nre[4], nim[4];
+                    // the record after this one: next quad of this chunk, else this
+                    // warp's first quad of the next chunk
+                    int hn = c * p.CH + qq + 2;
+                    if (qq + 2 >= nqc) hn = (c + 1) * p.CH + hh;
+                    const bool more = hn < p.nq;
+                    store(col, cre, cim);
+                    if (more) {
+                        record(hn, nre, nim);
 #pragma unroll
-                    for (int hb = 0; hb < 2; ++hb) {
-                        const uint32_t taddr = col + ((uint32_t)(32 * q + 16 * hb) << 16);
-                        const int p0 = 2 * hb, p1 = 2 * hb + 1;
-                        if constexpr (F32) {
-                            const f2 rl0 = tf32_lo(re[p0]), il0 = tf32_lo(im[p0]);
-                            const f2 rl1 = tf32_lo(re[p1]), il1 = tf32_lo(im[p1]);
-                            const uint32_t r[16] = {f2lo(re[p0]), f2hi(re[p0]), f2lo(re[p1]), f2hi(re[p1]),
-                                                    f2lo(im[p0]), f2hi(im[p0]), f2lo(im[p1]), f2hi(im[p1]),
-                                                    f2lo(rl0),    f2hi(rl0),    f2lo(rl1),    f2hi(rl1),
-                                                    f2lo(il0),    f2hi(il0),    f2lo(il1),    f2hi(il1)};
-                            tm_st_x4(taddr, r);
-                        } else {
-                            tm_st_x1(taddr, tm_pack16<PREC>(re[p0]), tm_pack16<PREC>(im[p0]),
-                                     tm_pack16<PREC>(re[p1]), tm_pack16<PREC>(im[p1]));
+                        for (int e = 0; e < 4; ++e) {
+                            cre[e] = nre[e];
+                            cim[e] = nim[e];
                         }
                     }
                 }
@@ -515,7 +566,8 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
         for (int j = 0; j < n_local; ++j) {
             int nf;
             const long long f0 = tile_frames(j, nf);
-            if (!warp_wait(&bar[kTbDFull], (unsigned)j & 1u, p.wait_cycles)) {
+            const int db = j & 1;
+            if (!warp_wait(&bar[kTbDFull + db], (unsigned)(j >> 1) & 1u, p.wait_cycles)) {
                 ok = false;
                 break;
             }
@@ -527,7 +579,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                 float v[32];
 #pragma unroll
                 for (int part = 0; part < DW / 32 + (DW % 32 ? 1 : 0); ++part) {
-                    const uint32_t taddr = tmem + lane_base + (uint32_t)(iw * DW + 32 * part);
+                    const uint32_t taddr = tmem + lane_base + (uint32_t)((db * p.NI + iw) * DW + 32 * part);
                     if constexpr (DW % 32 == 0) {
                         tm_ld32(taddr, v);
 #pragma unroll
@@ -541,7 +593,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&bar[kTbDEmpty]);
+            if (lane == 0) mbar_arrive(&bar[kTbDEmpty + db]);
             // coefficients in the packing of the CUDA-core kernel: zE = (sum pe Re x_s, sum pe Im x_s),
             // zO = (sum po Re x_d, sum po Im x_d)
             f2 zE[KH], zO[KH];
@@ -704,14 +756,17 @@ fcc_status_t prepare_tm(fcc_plan *plan)
     const int want_nba = eb ? atoi(eb) : 0, want_ch = ec ? atoi(ec) : 0;
     for (int NI = kTmMaxIss; NI >= 1 && !found; --NI) {
         if (want_ni && NI != want_ni) continue;
-        const int avail = kTmCols - NI * DW;
-        for (int NBA = std::min(kTmMaxA, NI + 2); NBA >= 2 && !found; --NBA) {
+        const int avail = kTmCols - 2 * NI * DW;
+        // NBA >= NI: the MMA warp of chunk g waits for fill g / NBA of its buffer only
+        // after finishing chunk g - NI, so fill g / NBA - 1 has completed and the
+        // parity of the wait is unambiguous
+        for (int NBA = std::min(kTmMaxA, NI + 1); NBA >= std::max(2, NI) && !found; --NBA) {
             if (want_nba && NBA != want_nba) continue;
-            int CH = avail / (NBA * CW);
-            CH = std::min(CH, 8);
-            if (CH >= 4) CH &= ~1;
+            // an even number of quads per chunk: the two producer warps of a lane
+            // quadrant take the even and the odd quads
+            int CH = std::min(avail / (NBA * CW), 8) & ~1;
             if (want_ch) {
-                if (want_ch > CH) continue;
+                if (want_ch > CH || (want_ch & 1)) continue;
                 CH = want_ch;
             }
             if (CH < 2) continue;

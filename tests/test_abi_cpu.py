@@ -112,7 +112,7 @@ def test_remaining_entry_points_reject_null_arguments(lib):
         lambda: lib.fcc_plan_geometry(N, N),
         lambda: lib.fcc_plan_autotune(N, N, 0, 1, N),
         lambda: lib.fcc_smooth_workspace(N, 10, N),
-        lambda: lib.fcc_tdoa_smoothed(N, N, 0, d(0.5), N, N, 0, N, N, N, N, N),
+        lambda: lib.fcc_tdoa_smoothed(N, N, 0, d(0.5), N, N, 0, N, N, N, N, N, N),
         lambda: lib.fcc_batch_create(N, N, 0, 0, 0, N, ctypes.byref(h)),
         lambda: lib.fcc_batch_info(N, N),
         lambda: lib.fcc_batch_array_info(N, 0, N),
