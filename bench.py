@@ -76,8 +76,16 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
 
 
 def rank_seed(rank: int) -> int:
-    """Each rank draws its own frames (disjoint scenes, same statistics)."""
+    """Seed of the scene segment a rank's frames come from (disjoint segments of
+    one scene, same statistics)."""
     return 2 + 7919 * rank
+
+
+def rank_frames(T: int, rank: int, world: int):
+    """Weak scaling: the job's scene has world * T frames and rank r takes the
+    contiguous slice binding.frame_range(world * T, r, world) of it."""
+    from paper_2204_13622_gb300 import binding
+    return binding.frame_range(world * T, rank, world)
 
 
 # ----------------------------------------------------------------------------
@@ -270,7 +278,8 @@ def run_fcc(args, rank, world, local):
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
-    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    t0, t1 = rank_frames(T, rank, world)  # this rank's slice of the job's frames
+    X = w.spectra(T=t1 - t0, device=dev, seed=rank_seed(rank))
     plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, prec=args.prec, engine=args.engine)
     out = plan.tdoa(X, tau_hat=True)  # allocates the outputs once
     stream = torch.cuda.current_stream(dev)
@@ -784,7 +793,8 @@ def run_doa(args, rank, world, local):
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
-    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    t0, t1 = rank_frames(T, rank, world)  # this rank's slice of the job's frames
+    X = w.spectra(T=t1 - t0, device=dev, seed=rank_seed(rank))
     plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, mic_xyz=w.xyz, device=local)
     dirs = synth.fibonacci_directions(args.dirs)
     doa = binding.Doa(plan, w.xyz, dirs)
@@ -877,7 +887,8 @@ def run_split_form(args, rank, world, local):
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
-    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    t0, t1 = rank_frames(T, rank, world)  # this rank's slice of the job's frames
+    X = w.spectra(T=t1 - t0, device=dev, seed=rank_seed(rank))
     plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, form="reim")
     out = plan.tdoa(X)
     stream = torch.cuda.current_stream(dev)
@@ -1040,7 +1051,8 @@ def run_smoothed(args, rank, world, local):
     torch.cuda.set_device(dev)
     distributed = dist_init(world, "nccl")
     T, P = (args.frames or w.T), w.P
-    X = w.spectra(T=T, device=dev, seed=rank_seed(rank))
+    t0, t1 = rank_frames(T, rank, world)  # this rank's slice of the job's frames
+    X = w.spectra(T=t1 - t0, device=dev, seed=rank_seed(rank))
     plan = binding.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, device=local, form=args.form)
     state = torch.zeros((P, w.B), dtype=torch.complex64, device=dev)
     work = torch.empty(max(plan.smooth_workspace(T), 8), dtype=torch.uint8, device=dev)

@@ -202,6 +202,18 @@ def _stream(stream, device):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def frame_range(T_total: int, rank: int, world: int):
+    """Frames [t0, t1) of rank `rank` when T_total frames are split across `world`
+    GPUs: contiguous, balanced (the first T_total % world ranks take one frame
+    more), together covering [0, T_total) once.  Frames are independent at
+    alpha = 1, so each rank runs fcc_tdoa on its own slice with no exchange."""
+    if world < 1 or not 0 <= rank < world or T_total < 0:
+        raise ValueError("need 0 <= rank < world and T_total >= 0")
+    base, extra = divmod(int(T_total), int(world))
+    t0 = rank * base + min(rank, extra)
+    return t0, t0 + base + (1 if rank < extra else 0)
+
+
 class Plan:
     """An FCC plan: lag grid, rank-K even/odd bases and kernel tables on one GPU."""
 
