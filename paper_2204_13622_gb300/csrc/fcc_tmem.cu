@@ -342,20 +342,30 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                                          : (PREC == FCC_PREC_BF16 ? ((1u << 7) | (1u << 10)) : 0u);
             constexpr uint32_t idesc = (1u << 4) | fmt | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             const uint32_t btab = smem_u32(smem + lay.btab);
-            long long g = 0;
+            // A buffer of the current chunk and the parity of its fill, advanced per chunk
+            int b = 0;
+            unsigned fpar = 0;
             bool ok = true, any = false;
             for (int j = 0; j < n_local && ok; ++j) {
                 bool first = true;
                 const int db = j & 1;  // D buffer of this tile: the epilogue runs a tile behind
                 const uint32_t d_re = tmem + (uint32_t)((db * p.NI + iw) * DW), d_im = d_re + 4 * KT;
-                for (int c = 0; c < n_ch; ++c, ++g) {
-                    if (c % p.NI != iw) continue;
+                int cw = 0;  // c % NI
+                for (int c = 0; c < n_ch; ++c) {
+                    const int bc = b;
+                    const unsigned pc = fpar;
+                    if (++b == p.NBA) {
+                        b = 0;
+                        fpar ^= 1u;
+                    }
+                    const bool mine = cw == iw;
+                    if (++cw == p.NI) cw = 0;
+                    if (!mine) continue;
                     if (first && !tm_wait(&bar[kTbDEmpty + db], ((unsigned)(j >> 1) & 1u) ^ 1u, p.wait_cycles)) {
                         ok = false;
                         break;
                     }
-                    const int b = (int)(g % p.NBA);
-                    if (!tm_wait(&bar[kTbAFull + b], (unsigned)(g / p.NBA) & 1u, p.wait_cycles)) {
+                    if (!tm_wait(&bar[kTbAFull + bc], pc, p.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -363,7 +373,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                     const int nqc = min(p.CH, p.nq - c * p.CH);
                     for (int qq = 0; qq < nqc; ++qq) {
                         const int h = c * p.CH + qq;
-                        const uint32_t acol = tmem + a0col + (uint32_t)((b * p.CH + qq) * CW);
+                        const uint32_t acol = tmem + a0col + (uint32_t)((bc * p.CH + qq) * CW);
                         const uint64_t bd = umma_desc(btab + (uint32_t)(h * p.bq), 128, 256);
                         const bool acc = !(first && qq == 0);
                         if constexpr (F32) {
@@ -375,7 +385,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                             tm_mma<1>(d_re, acol, bd, idesc, acc);
                         }
                     }
-                    umma_commit(&bar[kTbAEmpty + b]);
+                    umma_commit(&bar[kTbAEmpty + bc]);
                     first = false;
                     any = true;
                 }
@@ -398,7 +408,8 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
         Slot sl{};
         if (sidx < TS) sl = slots[sidx - fl * p.n_slots];
         const int RS = Q / 32;                        // records per lane in the PHAT
-        long long g = 0;
+        int b = 0;          // A buffer of the next chunk
+        unsigned fpar = 0;  // parity of that buffer's next fill
         bool ok = true;
         for (int j = 0; j < n_local && ok; ++j) {
             int nf;
@@ -491,51 +502,64 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                     im[pq] = fma2(nxr[ix], yi[iy], mul2(xi[ix], yr[iy]));
                 }
             };
-            auto store = [&](uint32_t col, const f2 (&re)[4], const f2 (&im)[4]) {
-#pragma unroll
-                for (int hb = 0; hb < 2; ++hb) {
-                    const uint32_t taddr = col + ((uint32_t)(32 * q + 16 * hb) << 16);
-                    const int p0 = 2 * hb, p1 = 2 * hb + 1;
-                    if constexpr (F32) {
-                        const f2 rl0 = tf32_lo(re[p0]), il0 = tf32_lo(im[p0]);
-                        const f2 rl1 = tf32_lo(re[p1]), il1 = tf32_lo(im[p1]);
-                        const uint32_t r[16] = {f2lo(re[p0]), f2hi(re[p0]), f2lo(re[p1]), f2hi(re[p1]),
-                                                f2lo(im[p0]), f2hi(im[p0]), f2lo(im[p1]), f2hi(im[p1]),
-                                                f2lo(rl0),    f2hi(rl0),    f2lo(rl1),    f2hi(rl1),
-                                                f2lo(il0),    f2hi(il0),    f2lo(il1),    f2hi(il1)};
-                        tm_st_x4(taddr, r);
-                    } else {
-                        tm_st_x1(taddr, tm_pack16<PREC>(re[p0]), tm_pack16<PREC>(im[p0]), tm_pack16<PREC>(re[p1]),
-                                 tm_pack16<PREC>(im[p1]));
-                    }
-                }
-            };
-            // ---- A chunks: the next record's loads and arithmetic run before the wait
-            // for the previous record's tensor-memory stores
-            f2 cre[4], cim[4];
-            record(hh, cre, cim);  // chunk 0, quad hh (every chunk holds at least two quads)
-            for (int c = 0; c < n_ch; ++c, ++g) {
-                const int b = (int)(g % p.NBA);
-                if (!warp_wait(&bar[kTbAEmpty + b], ((unsigned)(g / p.NBA) & 1u) ^ 1u, p.wait_cycles)) {
+            // ---- A chunks.  Per chunk a thread forms all of its records first (loads and
+            // arithmetic of up to RMAX records in flight), then stores them: tcgen05.st
+            // reads its source registers asynchronously, so no register it reads is
+            // rewritten before the chunk's wait::st.
+            constexpr int RMAX = F32 ? (KH > 4 ? 1 : 2) : 4;  // records per thread per chunk (CH <= 2 RMAX)
+            constexpr int VR = F32 ? 32 : 8;       // 32-bit values per record
+            for (int c = 0; c < n_ch; ++c) {
+                if (!warp_wait(&bar[kTbAEmpty + b], fpar ^ 1u, p.wait_cycles)) {
                     ok = false;
                     break;
                 }
                 const int nqc = min(p.CH, p.nq - c * p.CH);
-                for (int qq = hh; qq < nqc; qq += 2) {
-                    const uint32_t col = tmem + a0col + (uint32_t)((b * p.CH + qq) * CW);
-                    f2 nre[4], nim[4];
-                    // the record after this one: next quad of this chunk, else this
-                    // warp's first quad of the next chunk
-                    int hn = c * p.CH + qq + 2;
-                    if (qq + 2 >= nqc) hn = (c + 1) * p.CH + hh;
-                    const bool more = hn < p.nq;
-                    store(col, cre, cim);
-                    if (more) {
-                        record(hn, nre, nim);
+                uint32_t v[RMAX][VR];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            cre[e] = nre[e];
-                            cim[e] = nim[e];
+                for (int r = 0; r < RMAX; ++r) {
+                    const int qq = hh + 2 * r;
+                    if (qq < nqc) {
+                        f2 re[4], im[4];
+                        record(c * p.CH + qq, re, im);
+                        if constexpr (F32) {
+                            // per 16-lane half hb: pairs 2 hb and 2 hb + 1; groups (Re hi, Im hi, Re lo, Im lo)
+#pragma unroll
+                            for (int hb = 0; hb < 2; ++hb) {
+                                const int p0 = 2 * hb, p1 = 2 * hb + 1;
+                                const f2 rl0 = tf32_lo(re[p0]), il0 = tf32_lo(im[p0]);
+                                const f2 rl1 = tf32_lo(re[p1]), il1 = tf32_lo(im[p1]);
+                                uint32_t *o = v[r] + 16 * hb;
+                                o[0] = f2lo(re[p0]), o[1] = f2hi(re[p0]), o[2] = f2lo(re[p1]), o[3] = f2hi(re[p1]);
+                                o[4] = f2lo(im[p0]), o[5] = f2hi(im[p0]), o[6] = f2lo(im[p1]), o[7] = f2hi(im[p1]);
+                                o[8] = f2lo(rl0), o[9] = f2hi(rl0), o[10] = f2lo(rl1), o[11] = f2hi(rl1);
+                                o[12] = f2lo(il0), o[13] = f2hi(il0), o[14] = f2lo(il1), o[15] = f2hi(il1);
+                            }
+                        } else {
+#pragma unroll
+                            for (int pq = 0; pq < 4; ++pq) {
+                                v[r][2 * pq] = tm_pack16<PREC>(re[pq]);
+                                v[r][2 * pq + 1] = tm_pack16<PREC>(im[pq]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r) {
+                    const int qq = hh + 2 * r;
+                    if (qq < nqc) {
+                        const uint32_t col = tmem + a0col + (uint32_t)((b * p.CH + qq) * CW);
+#pragma unroll
+                        for (int hb = 0; hb < 2; ++hb) {
+                            const uint32_t taddr = col + ((uint32_t)(32 * q + 16 * hb) << 16);
+                            if constexpr (F32) {
+                                const uint32_t *o = v[r] + 16 * hb;
+                                const uint32_t rr[16] = {o[0], o[1], o[2],  o[3],  o[4],  o[5],  o[6],  o[7],
+                                                         o[8], o[9], o[10], o[11], o[12], o[13], o[14], o[15]};
+                                tm_st_x4(taddr, rr);
+                            } else {
+                                const uint32_t *o = v[r] + 4 * hb;
+                                tm_st_x1(taddr, o[0], o[1], o[2], o[3]);
+                            }
                         }
                     }
                 }
@@ -543,6 +567,10 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar[kTbAFull + b]);
+                if (++b == p.NBA) {
+                    b = 0;
+                    fpar ^= 1u;
+                }
             }
             if (!ok) break;
             __syncwarp();
@@ -764,7 +792,7 @@ fcc_status_t prepare_tm(fcc_plan *plan)
             if (want_nba && NBA != want_nba) continue;
             // an even number of quads per chunk: the two producer warps of a lane
             // quadrant take the even and the odd quads
-            int CH = std::min(avail / (NBA * CW), 8) & ~1;
+            int CH = std::min(avail / (NBA * CW), f32 ? (plan->kh > 4 ? 2 : 4) : 8) & ~1;
             if (want_ch) {
                 if (want_ch > CH || (want_ch & 1)) continue;
                 CH = want_ch;
