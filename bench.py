@@ -591,9 +591,9 @@ def run_precision(args, local, steps):
 
 
 def run_batched(args, rank, world, local):
-    """Batched form: 4096 independent arrays (mixed M, aperture, N, fs, T) in
-    per-class persistent launches captured in one CUDA graph; one step = one
-    graph launch over every frame and pair of every array."""
+    """Batched form: 4096 independent arrays (mixed M, aperture, N, fs, T) in one
+    persistent launch per kernel class (or one for the batch) captured in a CUDA
+    graph; one step = one graph launch over every frame and pair of every array."""
     import numpy as np
     import torch
 
@@ -604,7 +604,8 @@ def run_batched(args, rank, world, local):
     arrs = synth.batched_arrays(args.arrays, seed=4 + 7919 * rank)
     t0 = time.perf_counter()
     cache = os.environ.get("FCC_TUNE_CACHE") or os.path.join("/tmp", f"fcc_tune_{os.getpid()}.json")
-    batch = binding.Batch(arrs, device=local, autotune=args.autotune, tune_cache=cache)
+    batch = binding.Batch(arrs, device=local, autotune=args.autotune, tune_cache=cache,
+                          single_launch=args.batch_single_launch)
     t_create = time.perf_counter() - t0
     info = batch.info()
     need = info["spectra_bytes"] + 1.5 * info["pair_frames"] * 12
@@ -660,7 +661,8 @@ def run_batched(args, rank, world, local):
                "config": {"workload": f"batched: {args.arrays} arrays, M in {{2,4,6,8,12,16}}, aperture 2-8 cm, "
                                       "N in {256,512,1024}, fs in {16,48} kHz, 64-4096 frames each",
                           "arrays": info["n_arrays"], "frames": info["frames"], "pair_frames": info["pair_frames"],
-                          "classes": info["n_classes"], "jobs": info["n_jobs"], "bases": info["n_bases"],
+                          "classes": info["n_classes"], "launches": info["n_launches"], "jobs": info["n_jobs"],
+                          "bases": info["n_bases"],
                           "autotune": bool(args.autotune), "create_s": round(t_create, 2),
                           "l2": f"inputs ({info['spectra_bytes'] / 1e9:.1f} GB) larger than L2; no flush"},
                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -670,7 +672,7 @@ def run_batched(args, rank, world, local):
                "accuracy_vs_oracle": {"pair_frames": int(n_pf), "argmax_agreement": float(agree.mean())},
                "cpu_baseline": {"value": n_pf / t_or, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
                                 "sample": f"16 frames of 8 arrays ({n_pf} pair-frames), FP64 C oracle"},
-               "e2e": None, "gpu_launches": args.steps * info["n_classes"],
+               "e2e": None, "gpu_launches": args.steps * info["n_launches"],
                "step_ms": [round(x, 3) for x in per], "clocks": clk.summary()}
     batch.close()
     return res
@@ -1238,6 +1240,8 @@ def main(argv=None):
     ap.add_argument("--rooms", type=int, default=24, help="table1: simulated rooms per microphone spacing")
     ap.add_argument("--form", default="folded", choices=["folded", "reim"],
                     help="basis split: the paper's folded form, or cosine/sine bases on Re/Im")
+    ap.add_argument("--batch-single-launch", action="store_true",
+                    help="batched: one persistent launch for the whole batch instead of one per kernel class")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batched: keep the heuristic tile shapes (default: autotuned)")
     ap.add_argument("--train", type=int, default=10_000_000, help="learned: training pair-frames")

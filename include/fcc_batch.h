@@ -29,24 +29,35 @@ extern "C" {
 typedef struct fcc_batch fcc_batch_t;
 
 enum {
-    FCC_BATCH_AUTOTUNE = 1 /* time the tile shapes of every distinct (M, N, K, I) (see fcc_tune.h) */
+    FCC_BATCH_AUTOTUNE = 1,     /* time the tile shapes of every distinct (M, N, K, I) (see fcc_tune.h) */
+    FCC_BATCH_SINGLE_LAUNCH = 2 /* the whole batch as one persistent launch instead of one per kernel class */
 };
 
 typedef struct {
     int n_arrays;
-    int n_classes;       /* persistent launches in the graph */
+    int n_classes;       /* kernel classes (KH bases per parity, RS fold records per lane) among the arrays */
     int n_jobs;
     int n_bases;         /* distinct basis constructions (N, lag grid, K rule) */
     long long frames;    /* sum of T */
     long long pair_frames;
     double spectra_bytes; /* sum of T * M * (N/2+1) * 8: the bytes one run must read */
     double result_bytes;  /* sum of T * P * 8 (lag index + peak), plus 4 per pair-frame with tau_hat */
+    int n_launches;       /* persistent kernel launches in the graph: n_classes, or 1 with FCC_BATCH_SINGLE_LAUNCH */
 } fcc_batch_info_t;
 
 /*
  * Create plans for n_arrays arrays (descs[a].prec must be FCC_PREC_FP32; the
  * device field of every desc is ignored: all plans live on `device`, -1 =
- * current) with T[a] >= 1 frames each.  flags: FCC_BATCH_AUTOTUNE.  tune_cache:
+ * current) with T[a] >= 1 frames each.  flags: FCC_BATCH_AUTOTUNE,
+ * FCC_BATCH_SINGLE_LAUNCH.  By default the arrays are grouped into kernel classes
+ * (KH bases per parity, RS fold records per lane) and each class is one
+ * persistent launch with its own warp count and register budget, the classes
+ * being independent branches of one CUDA graph.  With FCC_BATCH_SINGLE_LAUNCH the
+ * whole batch is one persistent launch: its CTAs take (array, tile run) jobs of
+ * every array from one queue, largest first, and every array's tile geometry is
+ * limited to that kernel's eight compute warps (keeping the chunk count of the
+ * plan's own geometry).  Either way each array's results equal fcc_tdoa's on a
+ * plan of the same geometry bit for bit.  tune_cache:
  * as fcc_plan_autotune (NULL: FCC_TUNE_CACHE or none).  Synchronous.
  * Errors: INVALID_ARG (the message names the array), UNSUPPORTED, OOM, CUDA,
  * NOT_CONVERGED.

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfcc_gb300.so")
 OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["fcc_api.cu", "fcc_plan.cu", "fcc_fp32.cu", "fcc_fp32_reim.cu", "fcc_tc.cu", "fcc_gcc.cu", "fcc_mlp.cu", "fcc_tune.cu", "fcc_batch.cu",
-           "fcc_smooth.cu", "fcc_doa.cu", "fcc_stft.cu", "fcc_tmem.cu"]
+           "fcc_smooth.cu", "fcc_doa.cu", "fcc_stft.cu", "fcc_tmem.cu", "fcc_batch_all.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

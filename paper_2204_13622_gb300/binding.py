@@ -71,10 +71,11 @@ class Geometry(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_arrays", ctypes.c_int), ("n_classes", ctypes.c_int), ("n_jobs", ctypes.c_int),
                 ("n_bases", ctypes.c_int), ("frames", ctypes.c_longlong), ("pair_frames", ctypes.c_longlong),
-                ("spectra_bytes", ctypes.c_double), ("result_bytes", ctypes.c_double)]
+                ("spectra_bytes", ctypes.c_double), ("result_bytes", ctypes.c_double), ("n_launches", ctypes.c_int)]
 
 
 FCC_BATCH_AUTOTUNE = 1
+FCC_BATCH_SINGLE_LAUNCH = 2
 DEBUG_HOOKS = {"wait_cycles": 0, "withhold_copy": 1, "fail_alloc": 2}
 
 
@@ -686,13 +687,15 @@ _DESC_KEYS = ("n_mics", "fs", "N", "lag_den", "tau_max", "mic_xyz", "c", "K", "e
 
 
 class Batch:
-    """Many arrays in persistent launches under one CUDA graph (include/fcc_batch.h).
+    """Many arrays in persistent launches under one CUDA graph (include/fcc_batch.h):
+    one per kernel class, or one for the whole batch with single_launch=True.
 
     `arrays`: list of dicts with the Plan keywords (n_mics, fs, N, lag_den and
     optionally tau_max, mic_xyz, c, K, energy) plus T (frames); other keys are
     ignored."""
 
-    def __init__(self, arrays, device: int | None = None, autotune: bool = False, tune_cache: str | None = None):
+    def __init__(self, arrays, device: int | None = None, autotune: bool = False, tune_cache: str | None = None,
+                 single_launch: bool = False):
         import torch
         if device is None:
             device = torch.cuda.current_device()
@@ -706,7 +709,8 @@ class Batch:
             descs[a] = _desc(keep=keep, **kw)
             T[a] = int(d["T"])
         h = _vp()
-        check(lib().fcc_batch_create(descs, T, n, self.device, FCC_BATCH_AUTOTUNE if autotune else 0,
+        flags = (FCC_BATCH_AUTOTUNE if autotune else 0) | (FCC_BATCH_SINGLE_LAUNCH if single_launch else 0)
+        check(lib().fcc_batch_create(descs, T, n, self.device, flags,
                                      tune_cache.encode() if tune_cache else None, ctypes.byref(h)),
               "fcc_batch_create")
         self._h = h

@@ -1,12 +1,17 @@
 // fcc_batch.cu -- batched FCC over many independent arrays (include/fcc_batch.h).
 //
 // Host runtime: one FP32 plan per array (bases shared through the plan cache),
-// optional tile autotuning per distinct (M, N, K, I), arrays grouped into kernel
-// classes (KH, RS), jobs cut from each array's frame tiles and ordered largest
-// first, and one CUDA graph whose branches are the classes' persistent launches
-// (a memset of the class's job counter, then the launch).  Binding buffers only
-// rewrites the per-array parameter table the kernels read, so the graph is
-// captured once.
+// optional tile autotuning per distinct (M, N, K, I), jobs cut from each array's
+// frame tiles and ordered largest first, and one CUDA graph captured at create:
+//   * by default arrays grouped into kernel classes (KH, RS), one persistent
+//     launch per class (each with the class's own warp count and register
+//     budget), the classes as independent branches of the graph;
+//   * with FCC_BATCH_SINGLE_LAUNCH one persistent launch (fcc_batch_all.cu) whose
+//     CTAs take every job of every array from one queue; each job names its
+//     kernel instance (KH, RS), and the arrays' geometries are limited to that
+//     kernel's eight compute warps (one register budget, the largest class's).
+// Binding buffers only rewrites the per-array parameter table the kernels read,
+// so the graph is captured once.
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -20,8 +25,8 @@
 #include "fcc_internal.h"
 
 namespace fcc {
-fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int max_cand, double *us_out);
-bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us);
+fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int max_cand, double *us_out,
+                       int max_warps = 0);
 std::string tune_cache_path(const char *p);
 }  // namespace fcc
 
@@ -29,7 +34,7 @@ using namespace fcc;
 
 struct fcc_batch {
     struct Class {
-        int kh = 0, rs = 0, grid = 0, n_jobs = 0;
+        int kh = 0, rs = 0, grid = 0, n_jobs = 0;  // kh = 0: every array, the single launch
         size_t smem = 0;
         std::vector<int> arrays;
         BatchJob *d_jobs = nullptr;
@@ -48,6 +53,7 @@ struct fcc_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool bound = false;
+    bool single = false;  // one persistent launch for every array
     fcc_batch_info_t info{};
 };
 
@@ -96,7 +102,9 @@ std::vector<BatchJob> make_jobs(const fcc_batch *b, const fcc_batch::Class &c, i
         for (long long t0 = 0; t0 < n_tiles; t0 += even) {
             const long long nt = std::min(even, n_tiles - t0);
             const long long frames = std::min<long long>(nt * g.F, b->T[a] - t0 * g.F);
-            jobs.push_back({(double)frames * p->info.M * p->info.B * 8.0, BatchJob{a, (int)t0, (int)nt}});
+            const int rs = fp32_row_slots(p->info.Q);
+            const int code = 4 * (p->kh / 2 - 1) + (rs == 1 ? 0 : rs == 2 ? 1 : rs == 4 ? 2 : 3);
+            jobs.push_back({(double)frames * p->info.M * p->info.B * 8.0, BatchJob{a, (int)t0, (int)nt, code}});
         }
     }
     std::stable_sort(jobs.begin(), jobs.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
@@ -109,7 +117,8 @@ fcc_status_t capture_graph(fcc_batch *b)
 {
     for (auto &c : b->classes) {
         BatchParams bp{};
-        fcc_status_t st = launch_fp32_batch(c.kh, c.rs, bp, 0, 0, nullptr);  // prepare
+        fcc_status_t st = c.kh ? launch_fp32_batch(c.kh, c.rs, bp, 0, 0, nullptr)  // prepare
+                               : launch_fp32_batch_all(bp, 0, 0, nullptr);
         if (st != FCC_OK) return st;
     }
     FCC_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -121,7 +130,8 @@ fcc_status_t capture_graph(fcc_batch *b)
         if (e == cudaSuccess) e = cudaMemsetAsync(c.d_counter, 0, sizeof(int), c.stream);
         if (e == cudaSuccess) {
             BatchParams bp{b->d_arrays, c.d_jobs, c.n_jobs, c.d_counter};
-            st = launch_fp32_batch(c.kh, c.rs, bp, c.grid, c.smem, c.stream);
+            st = c.kh ? launch_fp32_batch(c.kh, c.rs, bp, c.grid, c.smem, c.stream)
+                      : launch_fp32_batch_all(bp, c.grid, c.smem, c.stream);
         }
         if (e == cudaSuccess && st == FCC_OK) e = cudaEventRecord(c.done, c.stream);
         if (e == cudaSuccess && st == FCC_OK) e = cudaStreamWaitEvent(b->cap, c.done, 0);
@@ -165,6 +175,8 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
     fcc_batch *b = new (std::nothrow) fcc_batch();
     if (!b) return fail(FCC_ERR_OOM, "host allocation");
     b->device = dev;
+    b->single = (flags & FCC_BATCH_SINGLE_LAUNCH) != 0;
+    const int cap = b->single ? kBatchAllWarps : 0;  // compute warps an array's geometry may use
     cudaError_t e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         free_batch(b);
@@ -196,7 +208,7 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
             std::snprintf(key, sizeof key, "%d|%d|%d|%d|%d", in.M, in.N, in.K_even, in.K_odd, in.I);
             auto it = tuned.find(key);
             if (it == tuned.end()) {
-                st = tune_fp32(p, cache, false, 0, nullptr);
+                st = tune_fp32(p, cache, false, 0, nullptr, cap);
                 if (st != FCC_OK) {
                     const std::string msg = "array " + std::to_string(a) + ": " + fcc_last_error();
                     free_batch(b);
@@ -209,6 +221,23 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
                     free_batch(b);
                     return st;
                 }
+            }
+        } else if (cap && p->geo.G * p->geo.GW > cap) {
+            // the single launch's eight warps: the best heuristic geometry within
+            // them, with the same chunk count (so the per-frame arithmetic, and the
+            // results, are those of fcc_tdoa with the plan's own geometry)
+            std::vector<Fp32Geometry> cand;
+            st = fp32_candidates(p, cand, cap);
+            const Fp32Geometry *pick = nullptr;
+            for (const Fp32Geometry &g : cand)
+                if (!pick && g.C == p->geo.C) pick = &g;
+            if (!pick && !cand.empty()) pick = &cand[0];
+            if (st == FCC_OK && !pick) st = fail(FCC_ERR_UNSUPPORTED, "no geometry within the batched kernel's warps");
+            if (st == FCC_OK) st = set_fp32_geometry(p, *pick);
+            if (st != FCC_OK) {
+                const std::string msg = "array " + std::to_string(a) + ": " + fcc_last_error();
+                free_batch(b);
+                return fail(st, msg);
             }
         }
     }
@@ -229,6 +258,13 @@ fcc_status_t fcc_batch_create(const fcc_plan_desc_t *descs, const long long *T, 
     fcc_batch_info_t &inf = b->info;
     inf.n_arrays = n_arrays;
     inf.n_classes = (int)b->classes.size();
+    inf.n_launches = b->single ? 1 : (int)b->classes.size();
+    if (b->single) {
+        fcc_batch::Class all;
+        for (int a = 0; a < n_arrays; ++a) all.arrays.push_back(a);
+        b->classes.clear();
+        b->classes.push_back(all);
+    }
     inf.n_bases = (int)bases.size();
     for (int a = 0; a < n_arrays; ++a) {
         const fcc_plan_info_t &in = b->plans[a]->info;

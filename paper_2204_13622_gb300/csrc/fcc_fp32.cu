@@ -125,7 +125,7 @@ fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t
 // one group, so every group sees a plain single-consumer ring and a phase parity
 // can never be stale.  The shared-memory budget leaves room for the batched
 // kernel's header, so one geometry serves both launch forms.
-fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out)
+fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out, int max_warps)
 {
     out.clear();
     const fcc_plan_info_t &in = plan->info;
@@ -139,7 +139,7 @@ fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &ou
     // basis row, padded to an odd number of 16-byte units: KH even then KH odd
     // weights (folded), or 2 KH float4 of cosine / sine weights (split form)
     const int BS = in.form == FCC_FORM_REIM_SPLIT ? 4 * (2 * kh + 1) : ((2 * kh / 4) % 2 == 0) ? 2 * kh + 4 : 2 * kh;
-    const int maxw = max_compute_warps(kh);
+    const int maxw = max_warps > 0 ? std::min(max_warps, max_compute_warps(kh)) : max_compute_warps(kh);
     std::vector<std::pair<double, Fp32Geometry>> scored;
     for (int C = 4; C <= 32 && C <= in.Q; C <<= 1) {
         const int SB = 32 / C;

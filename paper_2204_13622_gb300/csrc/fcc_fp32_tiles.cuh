@@ -105,23 +105,27 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
         nf = (int)min((long long)p.F, p.T - f0);
         return f0;
     };
-    // Issue the bulk copy of this CTA's tile k into its stage (group leader only).
+    // Issue the bulk copy of this CTA's tile k into its stage (group leader only);
+    // `inflight` marks the stages whose copy the leader has not yet seen land.
+    unsigned inflight = 0;
     auto issue = [&](int k) {
         int nf;
         const long long f0 = tile_src(k, nf);
         const int s = k % p.S;
         const unsigned bytes = (unsigned)nf * (unsigned)frame_bytes;
         mbar_arrive_expect_tx(&full[s], bytes);
+        inflight |= 1u << s;
         bulk_g2s(stages + (size_t)s * lay.stage_bytes,
                  reinterpret_cast<const unsigned char *>(p.spectra) + (size_t)f0 * frame_bytes, bytes, &full[s]);
     };
 
-    // prime this group's stages (the test hook withholds CTA 0's first copy, so
-    // that group's first wait runs out and the timeout path is taken)
+    // prime this group's stages (the test hook withholds the copy of the plan's
+    // first tile, so that group's first wait runs out and the timeout path is
+    // taken)
     const int Sg = p.S / p.G;
     if (p.bulk && leader)
         for (int j = 0; j < Sg; ++j)
-            if (group + j * p.G < n_local && !(p.inject && blockIdx.x == 0 && group == 0 && j == 0))
+            if (group + j * p.G < n_local && !(p.inject && tile_base == 0 && group == 0 && j == 0))
                 issue(group + j * p.G);
 
     // lane -> (frame in tile, slot, chunk).  A frame takes n_blocks whole warps;
@@ -156,6 +160,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             if (lane == 0) atomicOr(p.err, kErrTimeout);
             break;
         }
+        if (leader) inflight &= ~(1u << s);
 
         // ---- 2. PHAT + folded re-lay, one row per warp at a time
         {
@@ -561,10 +566,14 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             if (mine && gi == 0) emit(o, bi, best);
         }
     }
-    // never retire with one of this group's bulk copies still in flight
+    // never retire with one of this group's bulk copies still in flight: wait,
+    // with the full bound whatever the test hook set, for every copy that was
+    // issued and not yet seen landing (a withheld or never-issued tile has no
+    // copy to wait for)
     if (p.bulk && leader) {
         for (int k = k_done + p.G; k < n_local && k <= k_done + p.S; k += p.G)
-            if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u, p.wait_cycles)) atomicOr(p.err, kErrTimeout);
+            if ((inflight >> (k % p.S)) & 1u)
+                if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u, kWaitCycles)) atomicOr(p.err, kErrTimeout);
     }
 }
 

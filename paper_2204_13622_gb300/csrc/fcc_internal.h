@@ -111,7 +111,7 @@ struct Fp32Params {
     float *out_corr;        // nullable, [T][P][I]
     unsigned *err;
     long long wait_cycles;  // bound of every device-side wait (clock cycles)
-    int inject;             // test hook: 1 = CTA 0's first group withholds its first copy
+    int inject;             // test hook: 1 = the copy of the plan's first tile is withheld
 };
 
 // Batched FP32 form: one job = a run of consecutive tiles of one plan.
@@ -119,6 +119,7 @@ struct BatchJob {
     int array;    // index into BatchParams::arrays
     int tile0;    // first tile (F frames each, F from the array's geometry)
     int n_tiles;
+    int code;     // kernel instance of the array: 4 (KH / 2 - 1) + log2(RS)
 };
 
 struct BatchParams {
@@ -235,12 +236,17 @@ fcc_status_t finish_plan_bases(fcc_plan *plan, const std::vector<double> &Xe, co
                                const std::vector<double> &Je, const std::vector<double> &Jo, int K_req,
                                double energy);
 fcc_status_t choose_fp32_geometry(fcc_plan *plan);
-fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out);
+// max_warps > 0 keeps only geometries of at most that many compute warps.
+fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out, int max_warps = 0);
 // Set the plan's FP32 geometry and rebuild its device tables for it.
 fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g);
 Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                             float *tau, float *coef, float *corr, unsigned *err);
 fcc_status_t launch_fp32_batch(int kh, int rs, const BatchParams &bp, int grid, size_t smem, cudaStream_t st);
+// The single persistent launch of the batched form: every array of every kernel
+// class in one grid of kBatchAllWarps-warp CTAs (grid = 0 only prepares).
+constexpr int kBatchAllWarps = 8;
+fcc_status_t launch_fp32_batch_all(const BatchParams &bp, int grid, size_t smem, cudaStream_t st);
 int fp32_threads(int kh);
 int fp32_row_slots(int Q);
 fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx,

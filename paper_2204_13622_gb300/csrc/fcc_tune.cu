@@ -151,7 +151,7 @@ bool write_cache(const std::string &path, const std::map<std::string, Entry> &al
     return std::rename(tmp.c_str(), path.c_str()) == 0;
 }
 
-std::string tune_key(const fcc_plan *plan)
+std::string tune_key(const fcc_plan *plan, int max_warps)
 {
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, plan->device);
@@ -159,7 +159,9 @@ std::string tune_key(const fcc_plan *plan)
     char buf[512];
     std::snprintf(buf, sizeof buf, "fp32|%s|sms=%d|M=%d|N=%d|K=%d+%d|I=%d", prop.name, prop.multiProcessorCount,
                   in.M, in.N, in.K_even, in.K_odd, in.I);
-    return buf;
+    std::string k = buf;
+    if (max_warps > 0) k += "|warps<=" + std::to_string(max_warps);
+    return k;
 }
 
 // Synthetic spectra for timing: a fixed hash of the element index mapped to
@@ -179,7 +181,7 @@ __global__ void fill_kernel(float *x, long long n)
 
 // Looks the plan's key up in the cache; on a hit with a geometry that is still
 // a candidate, applies it.  Returns true on a hit.
-bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us)
+bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us, int max_warps)
 {
     if (path.empty()) return false;
     std::map<std::string, Entry> all;
@@ -187,12 +189,12 @@ bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us)
         std::lock_guard<std::mutex> lk(g_cache_mu);
         if (!read_cache(path, all)) return false;
     }
-    auto it = all.find(tune_key(plan));
+    auto it = all.find(tune_key(plan, max_warps));
     if (it == all.end()) return false;
     const Entry &e = it->second;
     auto get = [&](const char *k) { auto f = e.find(k); return f == e.end() ? -1 : (int)f->second; };
     std::vector<Fp32Geometry> cand;
-    if (fp32_candidates(plan, cand) != FCC_OK) return false;
+    if (fp32_candidates(plan, cand, max_warps) != FCC_OK) return false;
     Fp32Geometry want{get("C"), 0, 0, get("GW"), get("G"), get("F"), get("S"), 0, 0};
     for (const Fp32Geometry &g : cand)
         if (same_geometry(g, want)) {
@@ -206,13 +208,14 @@ bool tune_from_cache(fcc_plan *plan, const std::string &path, double *us)
     return false;
 }
 
-fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int max_cand, double *us_out)
+fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int max_cand, double *us_out,
+                       int max_warps)
 {
     if (plan->info.prec != FCC_PREC_FP32) return fail(FCC_ERR_INVALID_ARG, "autotune needs an FP32 plan");
     if (!plan->kh || plan->geo.G == 0) return fail(FCC_ERR_UNSUPPORTED, "no FP32 kernel for this plan");
-    if (!force && tune_from_cache(plan, path, us_out)) return FCC_OK;
+    if (!force && tune_from_cache(plan, path, us_out, max_warps)) return FCC_OK;
     std::vector<Fp32Geometry> cand;
-    fcc_status_t st = fp32_candidates(plan, cand);
+    fcc_status_t st = fp32_candidates(plan, cand, max_warps);
     if (st != FCC_OK) return st;
     // distinct launch shapes, best heuristic score first
     std::vector<Fp32Geometry> uniq;
@@ -300,7 +303,7 @@ fcc_status_t tune_fp32(fcc_plan *plan, const std::string &path, bool force, int 
         std::lock_guard<std::mutex> lk(g_cache_mu);
         std::map<std::string, Entry> all;
         read_cache(path, all);  // a missing or unreadable file starts empty
-        all[tune_key(plan)] = Entry{{"C", best.C},  {"GW", best.GW}, {"G", best.G},
+        all[tune_key(plan, max_warps)] = Entry{{"C", best.C},  {"GW", best.GW}, {"G", best.G},
                                     {"F", best.F},  {"S", best.S},   {"us_per_frame", best_us}};
         if (!write_cache(path, all)) return fail(FCC_ERR_INVALID_ARG, "cannot write the tuning cache " + path);
     }
@@ -335,7 +338,7 @@ fcc_status_t fcc_plan_autotune(fcc_plan_t *plan, const char *cache_path, int for
     if (plan->info.form != FCC_FORM_FOLDED) return fail(FCC_ERR_UNSUPPORTED, "the tuner times the folded-form kernel");
     DeviceScope scope(plan->device);
     if (!scope.ok) return fail(FCC_ERR_CUDA, "cudaSetDevice failed");
-    return tune_fp32(plan, tune_cache_path(cache_path), force != 0, max_candidates, us_per_frame);
+    return tune_fp32(plan, tune_cache_path(cache_path), force != 0, max_candidates, us_per_frame, 0);
 }
 
 }  // extern "C"

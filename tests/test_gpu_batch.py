@@ -54,6 +54,7 @@ def test_batch_equals_single_plans(B):
     batch = B.Batch(arrs)
     info = batch.info()
     assert info["n_arrays"] == 40 and info["n_classes"] >= 2
+    assert info["n_launches"] == info["n_classes"]  # one persistent launch per class
     assert info["frames"] == sum(a["T"] for a in arrs)
     X = [synth.array_spectra(a, device="cuda") for a in arrs]
     out = batch.outputs()
@@ -197,3 +198,27 @@ def test_autotune_ignores_a_corrupt_cache(B, tmp_path):
     data = json.load(open(cache))  # rewritten as a valid cache
     assert len(data["entries"]) == 1
     plan.close()
+
+
+def test_single_launch_equals_per_class_launches(B):
+    # FCC_BATCH_SINGLE_LAUNCH: every class in one persistent launch (geometries
+    # limited to its eight warps, same chunk counts); every array's results equal
+    # the per-class launches' bit for bit
+    arrs = _small_arrays(24, seed=11)
+    X = [synth.array_spectra(a, device="cuda") for a in arrs]
+    one = B.Batch(arrs, single_launch=True)
+    many = B.Batch(arrs)
+    assert one.info()["n_launches"] == 1
+    assert many.info()["n_launches"] == many.info()["n_classes"] >= 2
+    o1, o2 = one.outputs(), many.outputs()
+    one.bind(X, o1)
+    many.bind(X, o2)
+    one.run()
+    many.run()
+    one.sync()
+    many.sync()
+    for a in range(len(arrs)):
+        for k in ("lag_idx", "peak", "tau_hat"):
+            assert torch.equal(o1[a][k], o2[a][k]), (a, k)
+    one.close()
+    many.close()
