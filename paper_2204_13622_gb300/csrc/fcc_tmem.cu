@@ -342,15 +342,19 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                                          : (PREC == FCC_PREC_BF16 ? ((1u << 7) | (1u << 10)) : 0u);
             constexpr uint32_t idesc = (1u << 4) | fmt | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             const uint32_t btab = smem_u32(smem + lay.btab);
-            // A buffer of the current chunk and the parity of its fill, advanced per chunk
+            // A buffer of the current chunk and the parity of its fill, advanced per
+            // chunk.  Chunks go to the MMA warps round-robin over the whole sequence
+            // of chunks (not per tile), so a warp's consecutive chunks are exactly NI
+            // <= NBA apart: when it waits for fill k of a buffer, fill k - 1 has
+            // landed and the parity of the wait is unambiguous.
             int b = 0;
             unsigned fpar = 0;
+            int cw = 0;  // (global chunk index) % NI
             bool ok = true, any = false;
             for (int j = 0; j < n_local && ok; ++j) {
                 bool first = true;
                 const int db = j & 1;  // D buffer of this tile: the epilogue runs a tile behind
                 const uint32_t d_re = tmem + (uint32_t)((db * p.NI + iw) * DW), d_im = d_re + 4 * KT;
-                int cw = 0;  // c % NI
                 for (int c = 0; c < n_ch; ++c) {
                     const int bc = b;
                     const unsigned pc = fpar;
