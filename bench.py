@@ -1172,11 +1172,41 @@ def run_learned(args, rank, world, local):
     plan8.sync()
     mlp.sync()
     c8_ms = e0.elapsed_time(e1) / args.steps
+
+    # the chain's parts timed alone: FCC without and with the coefficient output,
+    # then the head on those coefficients.  The difference between the first two
+    # plus the head's reading of the coefficients is what the coefficients' trip
+    # through HBM costs.
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    fo = plan8.tdoa(Xc)
+    fcc_ms = timed(lambda: plan8.tdoa(Xc, out=fo))
+    fo["coeffs"] = lo["coeffs"]
+    fcc_coef_ms = timed(lambda: plan8.tdoa(Xc, out=fo))
+    feat, tfcc = lo["coeffs"].view(-1, 2 * plan8.K), lo["tau_fcc"].view(-1)
+    ho = {k: torch.empty(tfcc.numel(), device=dev) for k in ("tau", "conf", "raw")}
+    head_ms = timed(lambda: mlp.infer(feat, tfcc, th, out=ho))
+    plan8.sync()
+    mlp.sync()
+    coef_bytes = lo["coeffs"].numel() * 4
     c8 = {"workload": w.name if frames == w.T else f"{w.name} truncated to {frames} frames",
           "ms_per_step": c8_ms, "pair_frames_per_s": frames * w.P / (c8_ms / 1000.0),
           "head_share_of_pair_frames": float((lo["conf"] >= th).float().mean()),
-          "kernels": "fcc_fp32_kernel (with coefficients) + mlp_infer_tc_kernel"}
-    del Xc, lo
+          "kernels": "fcc_fp32_kernel (with coefficients) + mlp_infer_tc_kernel",
+          "parts_ms": {"fcc_tdoa": fcc_ms, "fcc_tdoa_with_coefficients": fcc_coef_ms, "head_alone": head_ms},
+          "coefficient_bytes": coef_bytes,
+          "coefficient_round_trip_ms_at_measured_hbm": 2 * coef_bytes / (_peak_hbm()[0] * 1e6),
+          "ratio_to_fcc_tdoa": c8_ms / fcc_ms}
+    del Xc, lo, fo, ho
     plan8.close()
     res = {"metric": "learned-head TDoA RMSE (samples) vs FCC + parabolic refinement", "unit": "samples",
            "value": r["rmse_mlp_gated"], "higher_is_better": False, "n_gpus": 1, "steps": args.steps,

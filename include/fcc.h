@@ -56,16 +56,17 @@ typedef enum {
 } fcc_prec_t;
 
 /*
- * Which kernel a plan runs fcc_tdoa on.  AUTO picks the tensor-memory kernel
- * where it applies (N in [128, 1024], an even number of mics, folded form),
- * else the CUDA-core kernel for FP32 plans and the shared-memory tensor-core
- * kernel for BF16 / FP16 plans.
+ * Which kernel a plan runs fcc_tdoa on.  AUTO picks the fastest measured one:
+ * the CUDA-core kernel for FP32 plans and the shared-memory tensor-core kernel
+ * for BF16 / FP16 plans.
  *   CUDA_CORES   the Eq. 9 projection in packed FP32 FMAs (FP32 plans only).
  *   TENSOR_TMEM  the Eq. 9 projection as tcgen05 MMAs whose A operand (the
  *                cross spectra) is written straight into tensor memory; FP32
  *                plans use TF32 with a two-term split of both operands, BF16 /
- *                FP16 plans one rounding of the cross spectra.
- *   TENSOR_SMEM  the 16-bit forms with the A operand staged in shared memory.
+ *                FP16 plans one rounding of the cross spectra.  Folded plans
+ *                with an even number of mics and 128 <= N <= 1024.
+ *   TENSOR_SMEM  the 16-bit forms with the A operand staged in shared memory
+ *                (BF16 / FP16 plans only).
  */
 typedef enum {
     FCC_ENGINE_AUTO = 0,

@@ -14,10 +14,9 @@
 //      the fold records l, l + 32, ... of its four pairs and keeps their
 //      smoothed R (both bins of each record, as R / alpha) in registers across
 //      the chunk's frames; per frame it updates R, applies the phase transform
-//      and folds (Eq. 8) into the warp's shared-memory rows.  Then lane (q, i)
-//      projects pair q's rows onto coefficient(s) i (Eqs. 7, 9) with no
-//      cross-lane reduction, and 8 lanes per pair reconstruct the lag grid,
-//      argmax and refinement as the FP32 path.
+//      and folds (Eq. 8) into the warp's shared-memory rows.  Then 8 lanes per
+//      pair project its rows onto the bases (Eqs. 7, 9), and 8 lanes per pair
+//      reconstruct the lag grid, argmax and refinement as the FP32 path.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -154,8 +153,10 @@ struct SmoothLayout {
 //   state    lane l owns records l, l + 32, ... (both bins f and N/2 - f) of the
 //            slot's four pairs and keeps their R in registers: Eq. 1 update,
 //            R_hat = R / |R|, fold (Eq. 8), x_s and x_d written to the warp's rows;
-//   project  lane (q, i) = (l / 8, l % 8) forms coefficient(s) i * CPL.. of pair q
-//            over all records (Eqs. 7, 9): no cross-lane reduction;
+//   project  8 lanes per pair q (Eqs. 7, 9): in the folded form lane (q, g, h)
+//            forms a quarter of the coefficients over half of the records, and
+//            lanes h = 0, 1 add with one shuffle; in the split form lane (q, i)
+//            forms coefficient(s) i * CPL.. over all bins;
 //   search   8 lanes per pair split the lag steps of the reconstruction, then
 //            argmax and refinement as the FP32 path.
 // R / |R| without a branch: R is first scaled by the power of two that brings
@@ -176,6 +177,29 @@ __device__ __forceinline__ f2 unit_scaled(float rx, float ry, bool &bad)
     return mul2(ab, pk(r, r));
 }
 
+// R / |R| without the scaling, valid when |R|^2 is a normal FP32 number; ok is
+// cleared otherwise (zero, tiny, huge or non-finite R), and the warp then redoes
+// the frame with unit_scaled.  In the normal range both give the same value: the
+// scaling is by a power of two, and |R|^2 by a power of four.
+__device__ __forceinline__ f2 unit_fast(f2 R, bool &ok)
+{
+    float rx, ry;
+    upk(R, rx, ry);
+    const float s = fmaf(rx, rx, ry * ry);
+    ok = ok && (s >= FLT_MIN) && (s <= FLT_MAX);
+    const float r = rsqrtf(s);
+    return mul2(R, pk(r, r));
+}
+
+// Eq. 1 on R / alpha: beta R + x y^*, with the cross spectrum
+// x y^* = (xr yr + xi yi, xi yr - xr yi) folded into the FMA chain.
+__device__ __forceinline__ f2 cross_update(f2 R, float2 x, float2 y, f2 beta2)
+{
+    float bx, by;
+    upk(mul2(beta2, R), bx, by);
+    return pk(fmaf(x.x, y.x, fmaf(x.y, y.y, bx)), fmaf(x.y, y.x, fmaf(-x.x, y.y, by)));
+}
+
 // FB (the split form): the rows hold R_hat at bins 0..N/2 unfolded, the
 // projection pairs the cosine weight with Re and the sine weight with Im in one
 // FFMA2 ((c_k, s_k) per coefficient), and the reconstruction table holds
@@ -183,7 +207,7 @@ __device__ __forceinline__ f2 unit_scaled(float rx, float ry, bool &bad)
 template <int KH, int RS, bool FB>
 __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constant__ SmoothParams p)
 {
-    constexpr int CPL = KH > 4 ? 2 : 1;  // coefficients per projecting lane
+    constexpr int CPL = KH > 4 ? 2 : 1;  // coefficients per projecting lane (split form)
     extern __shared__ __align__(128) unsigned char smem[];
     const SmoothLayout Ly(p.Q, KH, p.center, p.M, p.B, p.n_slots, FB);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);
@@ -195,7 +219,11 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
     const int frame_bytes = p.M * p.B * 8;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Q = p.Q, B = p.B, QP = Ly.QP;
+    // the host launches the instance with Q = 32 RS (N = 128 RS), so the row
+    // geometry of SmoothLayout is known here and addresses fold into immediates
+    constexpr int Q = 32 * RS, B = 2 * Q + 1;
+    constexpr int QP = FB ? (2 * Q + 4) : ((Q + 4) & ~3);
+    constexpr int ROWB = QP * 8 + 16;
     const unsigned FULLM = 0xffffffffu;
     const int nw = p.n_slots;  // one warp per slot
     if (threadIdx.x == 0) {
@@ -213,13 +241,13 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
     // the padding entries past the last record (bin) stay zero (their weights are zero too)
     const int used = FB ? 2 * Q + 1 : Q + 1, npad = QP - used;
     for (int e = lane; e < Ly.rows * npad; e += 32)
-        reinterpret_cast<float2 *>(wreg + (size_t)(e / npad) * Ly.row_bytes)[used + e % npad] = make_float2(0.f, 0.f);
+        reinterpret_cast<float2 *>(wreg + (size_t)(e / npad) * ROWB)[used + e % npad] = make_float2(0.f, 0.f);
     fence_proxy_async();
     __syncthreads();
 
     const Slot sl = slots[warp];
-    float2 *zbuf = reinterpret_cast<float2 *>(wreg + (size_t)Ly.rows * Ly.row_bytes);  // [4][2 KH]
-    f2 *Rl = reinterpret_cast<f2 *>(zbuf + 4 * 2 * KH);                 // [4], lane 0's
+    float2 *zbuf = reinterpret_cast<float2 *>(wreg + (size_t)Ly.rows * ROWB);  // [4][2 KH]
+    f2 *Rl = reinterpret_cast<f2 *>(zbuf + 4 * 2 * KH);                 // [4]: pair q's, kept by lane q
     bool bad = false, failed = false;
     // This CTA's frames as one sequence g = i * chunk + k over its chunks
     // c_i = blockIdx.x + i * gridDim.x (only the global last chunk can be short,
@@ -270,7 +298,7 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                 R[q][j][0] = mul2(ia2, pk(u.x, u.y));
                 R[q][j][1] = mul2(ia2, pk(v.x, v.y));
             }
-            if (lane == 0) {
+            if (lane == q) {  // the lane that updates pair q's lone bin
                 const float2 w = cs ? cs[Q] : make_float2(0.f, 0.f);
                 Rl[q] = mul2(ia2, pk(w.x, w.y));
             }
@@ -297,6 +325,16 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
 #pragma unroll
             for (int r = 0; r < 4; ++r) row[r] = reinterpret_cast<const float2 *>(st + (size_t)sl.mic[r] * B * 8);
             // ---- state: Eq. 1, phase transform, fold (Eq. 8)
+            auto put = [&](int q, int fp, f2 ua, f2 ub) {
+                if (FB) {
+                    reinterpret_cast<f2 *>(wreg + (size_t)q * ROWB)[fp] = ua;
+                    reinterpret_cast<f2 *>(wreg + (size_t)q * ROWB)[2 * Q - fp] = ub;
+                } else {
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * ROWB)[fp] = add2(ua, ub);
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * ROWB)[fp] = sub2(ua, ub);
+                }
+            };
+            bool ok = true;
 #pragma unroll
             for (int j = 0; j < RS; ++j) {
                 const int fp = lane + 32 * j;
@@ -310,52 +348,50 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float2 x0 = xf[q >> 1], x1 = xb[q >> 1], y0 = yf[q & 1], y1 = yb[q & 1];
-                    // x y^* = (xr yr + xi yi, xi yr - xr yi), as one FMUL2 + one FFMA2
-                    const f2 a = fma2(pk(x0.y, x0.x), pk(y0.y, -y0.y), mul2(pk(x0.x, x0.y), pk(y0.x, y0.x)));
-                    const f2 b = fma2(pk(x1.y, x1.x), pk(y1.y, -y1.y), mul2(pk(x1.x, x1.y), pk(y1.x, y1.x)));
-                    R[q][j][0] = fma2(beta2, R[q][j][0], a);
-                    R[q][j][1] = fma2(beta2, R[q][j][1], b);
-                    float r0x, r0y, r1x, r1y;
-                    upk(R[q][j][0], r0x, r0y);
-                    upk(R[q][j][1], r1x, r1y);
-                    const f2 ua = unit_scaled(r0x, r0y, bad), ub = unit_scaled(r1x, r1y, bad);
-                    if (FB) {
-                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[fp] = ua;
-                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[2 * Q - fp] = ub;
-                    } else {
-                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[fp] = add2(ua, ub);
-                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[fp] = sub2(ua, ub);
-                    }
+                    R[q][j][0] = cross_update(R[q][j][0], xf[q >> 1], yf[q & 1], beta2);
+                    R[q][j][1] = cross_update(R[q][j][1], xb[q >> 1], yb[q & 1], beta2);
+                    put(q, fp, unit_fast(R[q][j][0], ok), unit_fast(R[q][j][1], ok));
                 }
             }
-            if (lane == 0) {
-                // the lone bin N/4: x_s = R_hat(N/4), x_d = 0 (Eq. 8)
+            if (!__all_sync(FULLM, ok)) {
+                // some |R|^2 of the frame is not a normal FP32 number: the whole warp
+                // redoes the frame's phase transform in the scaled form
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 x = row[q >> 1][Q], y = row[2 + (q & 1)][Q];
-                    const f2 a = pk(fmaf(x.x, y.x, x.y * y.y), fmaf(x.y, y.x, -(x.x * y.y)));
-                    Rl[q] = fma2(beta2, Rl[q], a);
-                    float rx, ry;
-                    upk(Rl[q], rx, ry);
-                    if (FB) {
-                        reinterpret_cast<f2 *>(wreg + (size_t)q * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
-                    } else {
-                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * Ly.row_bytes)[Q] = unit_scaled(rx, ry, bad);
-                        reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * Ly.row_bytes)[Q] = 0ull;
+                for (int j = 0; j < RS; ++j)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float r0x, r0y, r1x, r1y;
+                        upk(R[q][j][0], r0x, r0y);
+                        upk(R[q][j][1], r1x, r1y);
+                        put(q, lane + 32 * j, unit_scaled(r0x, r0y, bad), unit_scaled(r1x, r1y, bad));
                     }
+            }
+            if (lane < 4) {
+                // the lone bin N/4, one pair per lane: x_s = R_hat(N/4), x_d = 0 (Eq. 8)
+                const int q = lane;
+                const float2 x = ((q & 2) ? row[1] : row[0])[Q], y = ((q & 1) ? row[3] : row[2])[Q];
+                const f2 r = cross_update(Rl[q], x, y, beta2);
+                Rl[q] = r;
+                float rx, ry;
+                upk(r, rx, ry);
+                const f2 u = unit_scaled(rx, ry, bad);
+                if (FB) {
+                    reinterpret_cast<f2 *>(wreg + (size_t)q * ROWB)[Q] = u;
+                } else {
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q) * ROWB)[Q] = u;
+                    reinterpret_cast<f2 *>(wreg + (size_t)(2 * q + 1) * ROWB)[Q] = 0ull;
                 }
             }
             // the stage is read: release it (thread 0 refills it at the next frame)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&freed[s]);
-            // ---- project (Eqs. 7, 9): lane (q, i) forms coefficients v0 .. v0 + CPL - 1
+            // ---- project (Eqs. 7, 9): lanes 8 q .. 8 q + 7 form pair q's coefficients
             {
                 const int q = lane >> 3, v0 = (lane & 7) * CPL;
                 if (FB && v0 < 2 * KH) {
                     // (c_k, s_k) += (w_c, w_s) * (Re R_hat, Im R_hat), two bins per 16-byte load
-                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)q * Ly.row_bytes);
+                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)q * ROWB);
                     f2 acc[CPL];
 #pragma unroll
                     for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0ull;
@@ -371,17 +407,22 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                     }
 #pragma unroll
                     for (int cc = 0; cc < CPL; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + v0 + cc] = acc[cc];
-                } else if (!FB && v0 < 2 * KH) {
-                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * q + (v0 >= KH)) * Ly.row_bytes);
-                    f2 acc[CPL];
+                } else if (!FB) {
+                    // lane (q, g, h): coefficients g CPH .. g CPH + CPH - 1 (g < 2: even
+                    // bases on x_s, else odd bases on x_d) of pair q over the record quads
+                    // h, h + 2, ...; the two halves add with one shuffle
+                    constexpr int CPH = KH / 2;
+                    const int g = (lane >> 1) & 3, h = lane & 1, w0 = g * CPH;
+                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * q + (w0 >= KH)) * ROWB);
+                    f2 acc[CPH];
 #pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) acc[cc] = 0ull;
+                    for (int cc = 0; cc < CPH; ++cc) acc[cc] = 0ull;
 #pragma unroll 4
-                    for (int r4 = 0; r4 < QP / 4; ++r4) {
+                    for (int r4 = h; r4 < QP / 4; r4 += 2) {
                         const float4 d0 = dat[2 * r4], d1 = dat[2 * r4 + 1];
 #pragma unroll
-                        for (int cc = 0; cc < CPL; ++cc) {
-                            const float4 w = reinterpret_cast<const float4 *>(basis + (size_t)(v0 + cc) * QP)[r4];
+                        for (int cc = 0; cc < CPH; ++cc) {
+                            const float4 w = reinterpret_cast<const float4 *>(basis + (size_t)(w0 + cc) * QP)[r4];
                             acc[cc] = fma2(pk(w.x, w.x), pk(d0.x, d0.y), acc[cc]);
                             acc[cc] = fma2(pk(w.y, w.y), pk(d0.z, d0.w), acc[cc]);
                             acc[cc] = fma2(pk(w.z, w.z), pk(d1.x, d1.y), acc[cc]);
@@ -389,7 +430,10 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
                         }
                     }
 #pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + v0 + cc] = acc[cc];
+                    for (int cc = 0; cc < CPH; ++cc) acc[cc] = add2(acc[cc], __shfl_xor_sync(FULLM, acc[cc], 1));
+                    if (h == 0)
+#pragma unroll
+                        for (int cc = 0; cc < CPH; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + w0 + cc] = acc[cc];
                 }
             }
             __syncwarp();
