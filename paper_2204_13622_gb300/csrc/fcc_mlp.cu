@@ -41,6 +41,48 @@ __device__ __forceinline__ float gelu_d(float a)
     return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
 }
 
+// GELU for the inference kernel, two values at a time in packed FP32:
+//   GELU(x) = x Phi(x) = max(x, 0) - t Phi(-t),  t = |x|,
+//   Phi(-t) = exp(-t^2 / 2) S(t),  S(t) = sum_j c_j u^j,  u = 1 / (1 + 0.3 t),
+// with t clamped to 7 (t Phi(-t) < 1e-11 beyond).  S(t) = Phi(-t) exp(t^2 / 2) is
+// smooth and slowly varying; c_0..c_7 are its least-squares fit on Chebyshev
+// points of u (csrc/fit_gelu.py, which also evaluates this order in FP32: the
+// error against the exact-erf GELU is below 5e-7, 1.4e-7 of max(1, |x|)).  One
+// reciprocal and one exp2 per value on the special-function unit, the rest in
+// packed FMAs.  The training kernels keep gelu() above.
+__device__ __forceinline__ float rcp_approx(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float a)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ f2 gelu2(float a, float b)
+{
+    const f2 t = pk(fminf(fabsf(a), 7.f), fminf(fabsf(b), 7.f));
+    float da, db;
+    upk(fma2(pk(0.3f, 0.3f), t, pk(1.f, 1.f)), da, db);
+    const f2 u = pk(rcp_approx(da), rcp_approx(db));
+    f2 s = pk(3.266900021e-02f, 3.266900021e-02f);
+    s = fma2(s, u, pk(-2.269355121e-01f, -2.269355121e-01f));
+    s = fma2(s, u, pk(4.993950225e-01f, 4.993950225e-01f));
+    s = fma2(s, u, pk(-3.028911948e-01f, -3.028911948e-01f));
+    s = fma2(s, u, pk(3.103419967e-01f, 3.103419967e-01f));
+    s = fma2(s, u, pk(5.813875278e-02f, 5.813875278e-02f));
+    s = fma2(s, u, pk(1.300175062e-01f, 1.300175062e-01f));
+    s = fma2(s, u, pk(-7.356064136e-04f, -7.356064136e-04f));
+    constexpr float kHalfLog2e = -0.72134752044448170f;  // -1 / (2 ln 2)
+    float qa, qb;
+    upk(mul2(mul2(t, pk(kHalfLog2e, kHalfLog2e)), t), qa, qb);
+    const f2 corr = mul2(mul2(t, pk(ex2_approx(qa), ex2_approx(qb))), s);
+    return sub2(pk(fmaxf(a, 0.f), fmaxf(b, 0.f)), corr);
+}
+
 struct MlpW {
     const __nv_bfloat16 *W1, *W2, *W3;  // BF16 copies: [H][nin], [H][H], [2][H]
     const float *b1, *b2, *b3;          // FP32
@@ -287,8 +329,9 @@ __global__ void mlp_adam_kernel(float *p, const float *g, float *m, float *v, lo
 // enter as a two-term BF16 split a = hi + lo (hi = bf16(a), lo = bf16(a - hi)),
 // so each layer is two MMA passes against the same BF16 weights and the
 // products carry the activations to about 2^-17 -- the FP32 activations of the
-// training kernels.  The epilogues read TMEM with tcgen05.ld (bias, exact-erf
-// GELU, the split for the next layer; layer 3 and the gate on the CUDA cores).
+// training kernels.  The epilogues read TMEM with tcgen05.ld (bias, GELU to
+// FP32 accuracy with gelu2, the split for the next layer; layer 3 and the gate
+// on the CUDA cores).
 constexpr int kTcRows = 128;
 constexpr int kTcThreads = 256;
 
@@ -333,16 +376,16 @@ __device__ __forceinline__ uint32_t bf2(float a, float b)
 // Write 8 consecutive K entries of row r (hi part at k, lo part at k + koff).
 __device__ __forceinline__ void store_split8(unsigned char *A, int r, int k, int K, int koff, const float *v)
 {
-    float hi[8], lo[8];
+    // hi = bf16(v) packed two at a time; its FP32 values are the packed halves
+    // moved to the top 16 bits, and lo = bf16(v - hi)
+    uint32_t hi[4], lo[4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        hi[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-        lo[j] = v[j] - hi[j];
+    for (int j = 0; j < 4; ++j) {
+        hi[j] = bf2(v[2 * j], v[2 * j + 1]);
+        lo[j] = bf2(v[2 * j] - __uint_as_float(hi[j] << 16), v[2 * j + 1] - __uint_as_float(hi[j] & 0xffff0000u));
     }
-    *reinterpret_cast<uint4 *>(A + kmaj(r, k, K)) =
-        make_uint4(bf2(hi[0], hi[1]), bf2(hi[2], hi[3]), bf2(hi[4], hi[5]), bf2(hi[6], hi[7]));
-    *reinterpret_cast<uint4 *>(A + kmaj(r, k + koff, K)) =
-        make_uint4(bf2(lo[0], lo[1]), bf2(lo[2], lo[3]), bf2(lo[4], lo[5]), bf2(lo[6], lo[7]));
+    *reinterpret_cast<uint4 *>(A + kmaj(r, k, K)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4 *>(A + kmaj(r, k + koff, K)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(MlpW w, const float *feat, const float *tau_fcc,
@@ -427,18 +470,53 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(MlpW w, const 
     };
 
     const long long n_tiles = (n + kTcRows - 1) / kTcRows;
+    // This thread's features of a tile: groups g of 8 at k = 8 half + 16 g (K1 is
+    // 16 or 32), loaded a tile ahead so that the loads overlap the tile's MMAs and
+    // epilogues; 16-byte loads where every row is 16-byte aligned.
+    const int ng = K1 / 16;
+    const bool vec = (nin % 4 == 0) && ((reinterpret_cast<uintptr_t>(feat) & 15) == 0);
+    float sc[2][8];
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * half + 16 * g + j;
+            sc[g][j] = (g < ng && k < nin) ? w.scale[k] : 0.f;
+        }
+    float xf[2][8];
+    auto load_feat = [&](long long tt) {
+        const long long s = tt * kTcRows + r;
+        const bool live = tt < n_tiles && s < n;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int k = 8 * half + 16 * g;
+            if (g < ng && live && vec && k + 8 <= nin) {
+                const float4 a = *reinterpret_cast<const float4 *>(feat + (size_t)s * nin + k);
+                const float4 b = *reinterpret_cast<const float4 *>(feat + (size_t)s * nin + k + 4);
+                xf[g][0] = a.x, xf[g][1] = a.y, xf[g][2] = a.z, xf[g][3] = a.w;
+                xf[g][4] = b.x, xf[g][5] = b.y, xf[g][6] = b.z, xf[g][7] = b.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    xf[g][j] = (g < ng && live && k + j < nin) ? feat[(size_t)s * nin + k + j] : 0.f;
+            }
+        }
+    };
+    load_feat(blockIdx.x);
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const long long s = t * kTcRows + r;
         const bool live = s < n;
         // ---- A of layer 1: scaled features split into hi | lo; the two halves
         // of the CTA take alternate groups of 8 features
-        for (int k = 8 * half; k < K1; k += 16) {
-            float x[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                x[j] = (live && k + j < nin) ? feat[(size_t)s * nin + k + j] * w.scale[k + j] : 0.f;
-            store_split8(A, r, k, 2 * K1, K1, x);
-        }
+        for (int g = 0; g < 2; ++g)
+            if (g < ng) {
+                float x[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) x[j] = xf[g][j] * sc[g][j];
+                store_split8(A, r, 8 * half + 16 * g, 2 * K1, K1, x);
+            }
+        load_feat(t + gridDim.x);
         if (!mma_and_wait(1)) {
             failed = true;
             break;
@@ -450,7 +528,11 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(MlpW w, const 
             float v[32];
             tmem_ld32(t_row + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1s[c + j]);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 bb = *reinterpret_cast<const float4 *>(b1s + c + j);
+                upk(gelu2(v[j] + bb.x, v[j + 1] + bb.y), v[j], v[j + 1]);
+                upk(gelu2(v[j + 2] + bb.z, v[j + 3] + bb.w), v[j + 2], v[j + 3]);
+            }
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_split8(A, r, c + j, 2 * kH, kH, v + j);
         }
@@ -466,10 +548,21 @@ __global__ void __launch_bounds__(kTcThreads) mlp_infer_tc_kernel(MlpW w, const 
             float v[32];
             tmem_ld32(t_row + c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float h = gelu(v[j] + b2s[c + j]);
-                y0 = fmaf(W3s[c + j], h, y0);
-                y1 = fmaf(W3s[kH + c + j], h, y1);
+            for (int j = 0; j < 32; j += 4) {
+                const float4 bb = *reinterpret_cast<const float4 *>(b2s + c + j);
+                const float4 w0 = *reinterpret_cast<const float4 *>(W3s + c + j);
+                const float4 w1 = *reinterpret_cast<const float4 *>(W3s + kH + c + j);
+                float h0, h1, h2, h3;
+                upk(gelu2(v[j] + bb.x, v[j + 1] + bb.y), h0, h1);
+                upk(gelu2(v[j + 2] + bb.z, v[j + 3] + bb.w), h2, h3);
+                y0 = fmaf(w0.x, h0, y0);
+                y1 = fmaf(w1.x, h0, y1);
+                y0 = fmaf(w0.y, h1, y0);
+                y1 = fmaf(w1.y, h1, y1);
+                y0 = fmaf(w0.z, h2, y0);
+                y1 = fmaf(w1.z, h2, y1);
+                y0 = fmaf(w0.w, h3, y0);
+                y1 = fmaf(w1.w, h3, y1);
             }
         }
         if (half == 1) {
