@@ -1,7 +1,8 @@
 // fcc_mlp.cu -- the learned TDoA head (an extension; the paper has no learned
 // part): a 2K -> 128 -> 128 -> 2 MLP on a pair-frame's projection coefficients,
-// y0 = sub-sample TDoA, y1 = confidence logit, exact erf GELU, BF16 weights,
-// FP32 accumulation and FP32 master weights for training.
+// y0 = sub-sample TDoA, y1 = confidence logit, exact erf GELU (erff in the
+// training kernels; a fitted form within 5e-7 of it in the inference kernel),
+// BF16 weights, FP32 accumulation and FP32 master weights for training.
 //
 // Kernels (hand-written, CUDA cores; one block = 128 threads, thread j <-> hidden
 // unit j, tiles of 32 samples):
