@@ -436,22 +436,36 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                     const float2 *xr = reinterpret_cast<const float2 *>(st + (size_t)R * B * 8);
                     float4 *rec = reinterpret_cast<float4 *>(ubuf + (size_t)R * p.us);
                     const int sw = tm_swz(R % M);
+                    // the fast form for the whole row first (independent records, so
+                    // their loads overlap), then one vote: a row with a zero, tiny,
+                    // huge or non-finite bin is redone in the careful form
+                    bool rok = true;
+#pragma unroll 4
                     for (int jj = 0; jj < RS; ++jj) {
                         const int fp = lane + 32 * jj;
                         bool o1, o2;
-                        float2 a = unit_phase_fast(xr[fp], o1);
-                        float2 b = unit_phase_fast(xr[2 * Q - fp], o2);
-                        if (!__all_sync(FULLM, o1 && o2)) {
-                            a = unit_phase_slow(xr[fp], bad);
-                            b = unit_phase_slow(xr[2 * Q - fp], bad);
-                        }
+                        const float2 a = unit_phase_fast(xr[fp], o1);
+                        const float2 b = unit_phase_fast(xr[2 * Q - fp], o2);
+                        rok = rok && o1 && o2;
                         rec[fp ^ sw] = make_float4(a.x, b.x, a.y, b.y);
                     }
                     if (lane == 0) {
                         bool o;
-                        float2 c = unit_phase_fast(xr[Q], o);
-                        if (!o) c = unit_phase_slow(xr[Q], bad);
+                        const float2 c = unit_phase_fast(xr[Q], o);
+                        rok = rok && o;
                         rec[Q ^ sw] = make_float4(c.x, 0.f, c.y, 0.f);
+                    }
+                    if (!__all_sync(FULLM, rok)) {
+                        for (int jj = 0; jj < RS; ++jj) {
+                            const int fp = lane + 32 * jj;
+                            const float2 a = unit_phase_slow(xr[fp], bad);
+                            const float2 b = unit_phase_slow(xr[2 * Q - fp], bad);
+                            rec[fp ^ sw] = make_float4(a.x, b.x, a.y, b.y);
+                        }
+                        if (lane == 0) {
+                            const float2 c = unit_phase_slow(xr[Q], bad);
+                            rec[Q ^ sw] = make_float4(c.x, 0.f, c.y, 0.f);
+                        }
                     }
                 }
                 if (__any_sync(FULLM, bad) && lane == 0) atomicOr(p.err, kErrNonFinite);
@@ -642,14 +656,26 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
             if (!(pq >= 0 && fl < nf)) continue;
             const size_t o = (size_t)(f0 + fl) * p.P + pq;
             float *corr = p.out_corr ? p.out_corr + o * p.I : nullptr;
-            float S, D;
-            eval_SD<KH>(recon, 0, zE, zO, S, D);
-            float best = S - D;
+            // the lag scan two steps at a time, each step's S and D over two
+            // partial sums (four independent FMA chains of KH instead of one of
+            // 2 KH); the steps are compared in increasing m as in eval_SD's scan
+            float best, S, D;
+            {
+                f2 e = 0ull, o = 0ull;
+                const float4 *g = reinterpret_cast<const float4 *>(recon);
+#pragma unroll
+                for (int k = 0; k < KH; ++k) {
+                    const float4 w = g[k];
+                    e = fma2(pk(w.x, w.y), zE[k], e);
+                    o = fma2(pk(w.z, w.w), zO[k], o);
+                }
+                upk(add2(e, o), S, D);
+            }
+            best = S - D;
             int bi = p.center;
             if (corr) corr[p.center] = best;
-            for (int m = 1; m <= p.center; ++m) {
-                eval_SD<KH>(recon, m, zE, zO, S, D);
-                const float ym = S + D, yp = S - D;  // y(center - m), y(center + m)
+            auto take = [&](int m, float Sm, float Dm) {
+                const float ym = Sm + Dm, yp = Sm - Dm;  // y(center - m), y(center + m)
                 if (ym >= best) {
                     best = ym;
                     bi = p.center - m;
@@ -662,6 +688,29 @@ __global__ void __launch_bounds__(kTmThreads, 1) fcc_tm_kernel(const __grid_cons
                     corr[p.center - m] = ym;
                     corr[p.center + m] = yp;
                 }
+            };
+            int m = 1;
+            for (; m + 1 <= p.center; m += 2) {
+                const float4 *g0 = reinterpret_cast<const float4 *>(recon + (size_t)m * 4 * KH);
+                const float4 *g1 = g0 + KH;
+                f2 e0 = 0ull, o0 = 0ull, e1 = 0ull, o1 = 0ull;
+#pragma unroll
+                for (int k = 0; k < KH; ++k) {
+                    const float4 w0 = g0[k], w1 = g1[k];
+                    e0 = fma2(pk(w0.x, w0.y), zE[k], e0);
+                    o0 = fma2(pk(w0.z, w0.w), zO[k], o0);
+                    e1 = fma2(pk(w1.x, w1.y), zE[k], e1);
+                    o1 = fma2(pk(w1.z, w1.w), zO[k], o1);
+                }
+                float S0, D0, S1, D1;
+                upk(add2(e0, o0), S0, D0);
+                upk(add2(e1, o1), S1, D1);
+                take(m, S0, D0);
+                take(m + 1, S1, D1);
+            }
+            if (m <= p.center) {
+                eval_SD<KH>(recon, m, zE, zO, S, D);
+                take(m, S, D);
             }
             p.out_idx[o] = bi;
             p.out_peak[o] = best;
