@@ -1226,8 +1226,10 @@ def run_learned(args, rank, world, local):
 def run_extras(args, local):
     """The default line's other workloads, each at its full size: the 16-mic
     grid in FP32 / BF16 / FP16 ("precision"), 4096 mixed arrays in one step
-    ("batched") and the learned head ("learned").  Each leg frees its device
-    memory before the next one starts."""
+    ("batched"), the learned head ("learned") and the headline workload from
+    int16 PCM through the STFT front-end, whose e2e leg moves 8x fewer bytes
+    over the host link than spectra ("pcm").  Each leg frees its device memory
+    before the next one starts."""
     import copy
 
     import torch
@@ -1246,6 +1248,10 @@ def run_extras(args, local):
     t0 = time.perf_counter()
     extras["learned"] = run_learned(a, 0, 1, local)
     extras["learned"]["wall_s"] = round(time.perf_counter() - t0, 1)
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    extras["pcm"] = run_pcm(a, 0, 1, local)
+    extras["pcm"]["wall_s"] = round(time.perf_counter() - t0, 1)
     torch.cuda.empty_cache()
     return extras
 
