@@ -48,7 +48,7 @@ def test_fitted_gelu_error_bound():
     err = np.abs(m.gelu_fp32(x, c).astype(np.float64) - exact)
     assert err.max() <= 5e-7
     assert (err / np.maximum(1.0, np.abs(x))).max() <= 1.5e-7
-    # special values: GELU(0) = 0, odd part x / 2 - GELU is even around 0
+    # special values: GELU(0) = 0, and GELU(x) - x / 2 is even: GELU(x) - GELU(-x) = x
     assert m.gelu_fp32(np.array([0.0]), c)[0] == 0.0
     xs = np.array([0.5, 1.0, 2.0, 3.0])
     g_pos, g_neg = m.gelu_fp32(xs, c).astype(np.float64), m.gelu_fp32(-xs, c).astype(np.float64)
