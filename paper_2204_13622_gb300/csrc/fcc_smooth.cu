@@ -14,9 +14,10 @@
 //      the fold records l, l + 32, ... of its four pairs and keeps their
 //      smoothed R (both bins of each record, as R / alpha) in registers across
 //      the chunk's frames; per frame it updates R, applies the phase transform
-//      and folds (Eq. 8) into the warp's shared-memory rows.  Then 8 lanes per
-//      pair project its rows onto the bases (Eqs. 7, 9), and 8 lanes per pair
-//      reconstruct the lag grid, argmax and refinement as the FP32 path.
+//      and folds (Eq. 8) into the warp's shared-memory rows.  Then each lane
+//      projects one row over a quarter of the records onto the bases of its
+//      parity (Eqs. 7, 9), and 8 lanes per pair reconstruct the lag grid,
+//      argmax and refinement as the FP32 path.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -37,7 +38,7 @@ struct SmoothParams {
     int chunk, n_chunks;    // frames per chunk
     float alpha, beta;      // beta = 1 - alpha
     const float2 *carry;    // [n_chunks][P][B]: the state entering each chunk
-    const float *basis;     // [2 KH][QP]: even bases' weights over records 0..Q, then odd (zero at Q and in the padding)
+    const float *basis;     // folded form: [2][QP / 2][KH / 2][4] (parity, record pair, two bases x two records); zero past K and Q
     const float *recon;     // [center + 1][KH][4]
     const Slot *slots;
     int center, I, KE, KO;
@@ -153,9 +154,11 @@ struct SmoothLayout {
 //   state    lane l owns records l, l + 32, ... (both bins f and N/2 - f) of the
 //            slot's four pairs and keeps their R in registers: Eq. 1 update,
 //            R_hat = R / |R|, fold (Eq. 8), x_s and x_d written to the warp's rows;
-//   project  8 lanes per pair q (Eqs. 7, 9): in the folded form lane (q, g, h)
-//            forms a quarter of the coefficients over half of the records, and
-//            lanes h = 0, 1 add with one shuffle; in the split form lane (q, i)
+//   project  (Eqs. 7, 9) in the folded form lane (rq, q, par) takes pair q's
+//            x_s (par 0) or x_d (par 1) row over record pairs rq, rq + 4, ...
+//            against all KH bases of that parity (each row element read once;
+//            the shared-memory pipe is this pass's bound), and the four record
+//            quarters add with two shuffles; in the split form lane (q, i)
 //            forms coefficient(s) i * CPL.. over all bins;
 //   search   8 lanes per pair split the lag steps of the reconstruction, then
 //            argmax and refinement as the FP32 path.
@@ -408,32 +411,37 @@ __global__ void __launch_bounds__(256, 2) fcc_smooth_kernel(const __grid_constan
 #pragma unroll
                     for (int cc = 0; cc < CPL; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + v0 + cc] = acc[cc];
                 } else if (!FB) {
-                    // lane (q, g, h): coefficients g CPH .. g CPH + CPH - 1 (g < 2: even
-                    // bases on x_s, else odd bases on x_d) of pair q over the record quads
-                    // h, h + 2, ...; the two halves add with one shuffle
-                    constexpr int CPH = KH / 2;
-                    const int g = (lane >> 1) & 3, h = lane & 1, w0 = g * CPH;
-                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * q + (w0 >= KH)) * ROWB);
-                    f2 acc[CPH];
+                    // lane (rq, qq, par): pair qq's row of parity par (x_s or x_d) over the
+                    // record pairs u = rq, rq + 4, ... against all KH bases of that parity,
+                    // so each row element is read once; a quarter-warp shares its record
+                    // pairs, whose weights (grouped per record pair) it reads in one
+                    // wavefront; the four record quarters add with two shuffles
+                    const int rq = lane >> 3, qq = (lane >> 1) & 3, par = lane & 1;
+                    const float4 *dat = reinterpret_cast<const float4 *>(wreg + (size_t)(2 * qq + par) * ROWB);
+                    const float4 *wv = reinterpret_cast<const float4 *>(basis) + (size_t)par * (QP / 2) * (KH / 2);
+                    f2 acc[KH];
 #pragma unroll
-                    for (int cc = 0; cc < CPH; ++cc) acc[cc] = 0ull;
-#pragma unroll 4
-                    for (int r4 = h; r4 < QP / 4; r4 += 2) {
-                        const float4 d0 = dat[2 * r4], d1 = dat[2 * r4 + 1];
+                    for (int k = 0; k < KH; ++k) acc[k] = 0ull;
+#pragma unroll 2
+                    for (int u = rq; u < QP / 2; u += 4) {
+                        const float4 d = dat[u];  // records 2u, 2u + 1 as (re, im, re, im)
+                        const f2 d0 = pk(d.x, d.y), d1 = pk(d.z, d.w);
 #pragma unroll
-                        for (int cc = 0; cc < CPH; ++cc) {
-                            const float4 w = reinterpret_cast<const float4 *>(basis + (size_t)(w0 + cc) * QP)[r4];
-                            acc[cc] = fma2(pk(w.x, w.x), pk(d0.x, d0.y), acc[cc]);
-                            acc[cc] = fma2(pk(w.y, w.y), pk(d0.z, d0.w), acc[cc]);
-                            acc[cc] = fma2(pk(w.z, w.z), pk(d1.x, d1.y), acc[cc]);
-                            acc[cc] = fma2(pk(w.w, w.w), pk(d1.z, d1.w), acc[cc]);
+                        for (int k2 = 0; k2 < KH / 2; ++k2) {
+                            // (w_{2k2}(2u), w_{2k2}(2u+1), w_{2k2+1}(2u), w_{2k2+1}(2u+1))
+                            const float4 w = wv[(size_t)u * (KH / 2) + k2];
+                            acc[2 * k2] = fma2(pk(w.y, w.y), d1, fma2(pk(w.x, w.x), d0, acc[2 * k2]));
+                            acc[2 * k2 + 1] = fma2(pk(w.w, w.w), d1, fma2(pk(w.z, w.z), d0, acc[2 * k2 + 1]));
                         }
                     }
 #pragma unroll
-                    for (int cc = 0; cc < CPH; ++cc) acc[cc] = add2(acc[cc], __shfl_xor_sync(FULLM, acc[cc], 1));
-                    if (h == 0)
+                    for (int k = 0; k < KH; ++k) {
+                        acc[k] = add2(acc[k], __shfl_xor_sync(FULLM, acc[k], 8));
+                        acc[k] = add2(acc[k], __shfl_xor_sync(FULLM, acc[k], 16));
+                    }
 #pragma unroll
-                        for (int cc = 0; cc < CPH; ++cc) reinterpret_cast<f2 *>(zbuf)[q * 2 * KH + w0 + cc] = acc[cc];
+                    for (int k = 0; k < KH; ++k)
+                        if ((k & 3) == rq) reinterpret_cast<f2 *>(zbuf)[qq * 2 * KH + par * KH + k] = acc[k];
                 }
             }
             __syncwarp();
@@ -615,11 +623,17 @@ fcc_status_t prepare_per_pair(fcc_plan *plan)
     const fcc_plan_info_t &in = plan->info;
     const int kh = plan->kh, Q = in.Q;
     const SmoothLayout Ly(Q, kh, in.center, in.M, in.B, plan->n_slots, false);
+    // [parity][record pair u][k / 2][(k, 2u), (k, 2u + 1), (k + 1, 2u), (k + 1, 2u + 1)]:
+    // the kernel's lane reads one float4 per two bases and two records
     std::vector<float> bas((size_t)2 * kh * Ly.QP, 0.f);
+    auto put = [&](int par, int k, int f, double w) {
+        const int u = f / 2, r = f % 2;
+        bas[(((size_t)par * (Ly.QP / 2) + u) * (kh / 2) + k / 2) * 4 + (k % 2) * 2 + r] = (float)w;
+    };
     for (int k = 0; k < in.K_even; ++k)
-        for (int f = 0; f <= Q; ++f) bas[(size_t)k * Ly.QP + f] = (float)plan->Pe[(size_t)k * (Q + 1) + f];
+        for (int f = 0; f <= Q; ++f) put(0, k, f, plan->Pe[(size_t)k * (Q + 1) + f]);
     for (int k = 0; k < in.K_odd; ++k)
-        for (int f = 0; f < Q; ++f) bas[(size_t)(kh + k) * Ly.QP + f] = (float)plan->Po[(size_t)k * Q + f];
+        for (int f = 0; f < Q; ++f) put(1, k, f, plan->Po[(size_t)k * Q + f]);
     float *d = nullptr;
     FCC_CUDA_TRY(dev_alloc((void **)&d, bas.size() * sizeof(float)));
     cudaError_t e = cudaMemcpy(d, bas.data(), bas.size() * sizeof(float), cudaMemcpyHostToDevice);
