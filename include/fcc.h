@@ -207,6 +207,10 @@ fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, doub
  *              (must be NULL for the split form: UNSUPPORTED).
  *   d_corr     device float [T][P][I]: the correlation y on the grid; or NULL.
  *   stream     cudaStream_t or NULL.
+ * Sizes the kernels take: FP32 plans N <= 1024, BF16 / FP16 plans
+ * 128 <= N <= 1024, and at most 8 bases of each parity; other plans return
+ * UNSUPPORTED here (their bases, fcc_gcc_tdoa and the smoothed path, within its
+ * own limits, still work).
  * Asynchronous; allocates nothing.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
  */
 fcc_status_t fcc_tdoa(fcc_plan_t *plan, const void *d_spectra, long long T, int *d_lag_idx,
