@@ -53,12 +53,15 @@ def _check(out, ref, R_gpu=None, R_ref=None):
         assert np.quantile(err, 0.999) <= 1e-4 and np.abs(R_gpu - R_end).max() <= 1e-4 * np.abs(R_end).max()
 
 
-@pytest.mark.parametrize("M,N,den,L,T,alpha", [(8, 512, 4, 5, 300, 0.1), (8, 512, 4, 5, 97, 0.5),
-                                               (4, 256, 4, 3, 261, 0.1), (2, 128, 2, 2, 150, 0.05),
-                                               (6, 512, 4, 3, 130, 0.3)])
-def test_smoothed_matches_oracle(B, O, M, N, den, L, T, alpha):
+@pytest.mark.parametrize("M,N,den,L,T,alpha,K", [(8, 512, 4, 5, 300, 0.1, 0), (8, 512, 4, 5, 97, 0.5, 0),
+                                               (4, 256, 4, 3, 261, 0.1, 0), (2, 128, 2, 2, 150, 0.05, 0),
+                                               (6, 512, 4, 3, 130, 0.3, 0), (4, 512, 2, 8, 120, 0.2, 0),
+                                               (4, 256, 4, 6, 77, 0.1, 16)])
+def test_smoothed_matches_oracle(B, O, M, N, den, L, T, alpha, K):
+    # the last two cases take 6 and 8 bases of each parity (K = 11 by the energy
+    # rule, and K = 16 given)
     X = _spectra(T, M, N, seed=M * 100 + T)
-    plan = B.Plan(M, 16000.0, N, den, tau_max=L)
+    plan = B.Plan(M, 16000.0, N, den, tau_max=L, K=K)
     P, Bn = plan.P, plan.B
     R0 = _state(P, Bn, seed=T, scale=2.0)
     state = torch.from_numpy(R0).cuda()
