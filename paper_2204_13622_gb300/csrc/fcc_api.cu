@@ -221,6 +221,7 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_err);
     cudaFree(p->d_tc_bases);
     cudaFree(p->d_tc_peq);
+    cudaFree(p->d_tc_rbases);
     cudaFree(p->d_tm_btab);
     cudaFree(p->d_smooth_basis);
     cudaFree(p->d_stft_tab);

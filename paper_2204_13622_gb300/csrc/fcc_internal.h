@@ -143,6 +143,9 @@ struct TcParams {
     float delta;
     const void *bases;      // 2 parts x [16][2Q] 16-bit, K-major core matrices
     const float *peq;       // [8]: even bases at bin N/4
+    const void *rbases;     // lag-grid tables for the reconstruction on the tensor cores:
+                            // [S hi, S lo, D hi, D lo][npad][16] FP16, K-major core matrices
+    int npad;               // lag steps 0..center rounded up to 16; 0: the CUDA-core scan
     const float *recon;     // as in Fp32Params
     const Slot *slots;
     int *out_idx;
@@ -221,6 +224,8 @@ struct fcc_plan {
     void *pcm_state = nullptr;         // fcc_tdoa_pcm_host staging, created on first use
     void *d_tc_bases = nullptr;
     float *d_tc_peq = nullptr;
+    void *d_tc_rbases = nullptr;       // reconstruction tables of the tensor-core path (or null)
+    int tc_npad = 0;
     int tc_F = 0;
     size_t tc_smem = 0;
     // tensor-memory path (fcc_tmem.cu)
