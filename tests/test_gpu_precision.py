@@ -118,3 +118,35 @@ def test_unsupported_sizes_are_rejected(B):
     assert e.value.status == 2
     with pytest.raises(B.FccError):
         B.Plan(5, 16000.0, 512, 4, tau_max=3, prec="fp16")
+
+
+@pytest.mark.parametrize("prec,min_agree,max_peak_err", [("bf16", 0.995, 3e-4), ("fp16", 0.999, 5e-5)])
+def test_grid16_full_size_sampled(B, prec, min_agree, max_peak_err):
+    """The 16-mic grid at its full 2^18 frames in one call (the bench's launch):
+    frames sampled across the run (first, last, random) against the FP64
+    oracle, argmax agreement on clear peaks and the median peak error.  On this
+    grid (97 lag steps) the reconstruction itself runs on the tensor cores."""
+    from oracle import oracle as O
+    w = workloads.GRID16
+    X = w.spectra(device="cuda", seed=2)
+    plan = B.Plan(w.M, w.fs, w.N, w.lag_den, tau_max=w.L, prec=prec)
+    out = plan.tdoa(X)
+    plan.sync()
+    rng = np.random.default_rng(1)
+    frames = np.unique(np.concatenate([[0, 1, w.T - 1], rng.integers(0, w.T, 96)]))
+    sel = torch.from_numpy(frames).cuda()
+    Xs = X[sel].cpu().numpy()
+    ref = O.Basis(w.N, w.L, w.lag_den, K=plan.K)
+    idx, peak, _, y = O.tdoa(Xs, ref.WK, ref.taus, ref.delta, want_y=True)
+    gi = out["lag_idx"][sel].cpu().numpy()
+    srt = np.sort(y, axis=-1)
+    scale = np.abs(y).max(-1)
+    clear = (srt[..., -1] - srt[..., -2]) > 1e-3 * scale
+    agree = float((gi == idx)[clear].mean())
+    perr = float(np.median(np.abs(out["peak"][sel].cpu().numpy() - peak) / scale))
+    print(f"{prec}: {int(clear.sum())} clear pair-frames, agreement {agree:.4f}, median peak error {perr:.2e}")
+    assert agree >= min_agree
+    assert perr <= max_peak_err
+    plan.close()
+    del X
+    torch.cuda.empty_cache()
