@@ -1,5 +1,6 @@
 // fcc_api.cu -- the extern "C" entry points declared in include/fcc.h.
 #include <algorithm>
+#include <cuda_fp16.h>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -164,6 +165,48 @@ void pack_tables(const fcc_plan *plan, std::vector<float> &basis, std::vector<fl
 
 }  // namespace
 
+// FP16 weight tables of the lag-grid reconstruction on the tensor cores,
+// [S part 0 .. parts-1, D part 0 .. parts-1][npad][16] in K-major 8 x 8 core
+// matrices: row n holds the weights of lag step m = m0 + n on (Re zE[0..7],
+// Re zO[0..7]) for S and on the imaginary parts for D (S = sum 2a Ue Re zE -
+// 2b Uo Re zO, D = sum 2b Ue Im zE + 2a Uo Im zO at tau = m / den, a =
+// cos(pi tau / 2), b = sin(pi tau / 2)), so that y(center -/+ m) = S +/- D.
+// Each weight, scaled by 2^shift, is split into `parts` FP16 terms (part 0 =
+// fp16(w), each next part the FP16 rounding of what is left).  Rows past the
+// grid's last lag step are zero.
+std::vector<uint16_t> recon_tables_f16(const fcc_plan *plan, int npad, int m0, int shift, int parts)
+{
+    const fcc_plan_info_t &in = plan->info;
+    const int KE = in.K_even, KO = in.K_odd;
+    std::vector<uint16_t> rt((size_t)2 * parts * npad * 16, 0);
+    const double sc = std::ldexp(1.0, shift);
+    auto put = [&](int t, int n, int k, double w) {
+        double v = w * sc;
+        const size_t off = (((size_t)(n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + (k % 8));
+        for (int q = 0; q < parts; ++q) {
+            const __half h = __float2half_rn((float)v);
+            rt[(size_t)(t * parts + q) * npad * 16 + off] = *reinterpret_cast<const uint16_t *>(&h);
+            v -= (double)__half2float(h);
+        }
+    };
+    for (int n = 0; n < npad && m0 + n <= in.center; ++n) {
+        const int m = m0 + n, i = in.center + m;
+        const double ang = M_PI * 0.5 * (double)m / (double)in.den;
+        const double a = std::cos(ang), b = std::sin(ang);
+        for (int k = 0; k < KE && k < 8; ++k) {
+            const double u = plan->Ue[(size_t)i * KE + k];
+            put(0, n, k, 2.0 * a * u);
+            put(1, n, k, 2.0 * b * u);
+        }
+        for (int k = 0; k < KO && k < 8; ++k) {
+            const double u = plan->Uo[(size_t)i * KO + k];
+            put(0, n, 8 + k, -2.0 * b * u);
+            put(1, n, 8 + k, 2.0 * a * u);
+        }
+    }
+    return rt;
+}
+
 fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g)
 {
     plan->geo = g;
@@ -222,6 +265,7 @@ void free_plan(fcc_plan *p)
     cudaFree(p->d_tc_bases);
     cudaFree(p->d_tc_peq);
     cudaFree(p->d_tc_rbases);
+    cudaFree(p->d_fp32_rbases);
     cudaFree(p->d_tm_btab);
     cudaFree(p->d_smooth_basis);
     cudaFree(p->d_stft_tab);
@@ -410,6 +454,7 @@ fcc_status_t fcc_plan_create(const fcc_plan_desc_t *d, fcc_plan_t **out)
         return cuda_fail(e, "plan tables");
     }
     if (in.form == FCC_FORM_FOLDED && in.prec == FCC_PREC_FP32 && p->kh) st = prepare_per_pair(p);
+    if (st == FCC_OK && in.form == FCC_FORM_FOLDED && p->kh >= 6) st = prepare_fp32_mma(p);
     if (st == FCC_OK) st = prepare_stft(p);
     if (st != FCC_OK) {
         free_plan(p);

@@ -35,6 +35,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdlib>
+#include <vector>
 
 #include "fcc_device.cuh"
 #include "fcc_internal.h"
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_kernel
     const int n_local = (p.n_tiles > (int)blockIdx.x)
                             ? (p.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                             : 0;
-    fp32_tiles<KH, RS, false>(p, smem, blockIdx.x, gridDim.x, n_local);
+    fp32_tiles<KH, RS, false, true>(p, smem, blockIdx.x, gridDim.x, n_local);
 }
 
 // Batched form: many plans of one (KH, RS) class in one persistent launch.  A
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(max_compute_warps(KH) * 32, 1) fcc_fp32_batch_
 }
 
 template <int KH, int RS>
-fcc_status_t launch_inst(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
+fcc_status_t launch_inst(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid, size_t smem)
 {
     static bool attr_set[64] = {};
     const int dev = plan->device;
@@ -98,21 +99,21 @@ fcc_status_t launch_inst(const fcc_plan *plan, const Fp32Params &prm, cudaStream
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fcc_fp32_kernel)");
         attr_set[dev & 63] = true;
     }
-    fcc_fp32_kernel<KH, RS><<<grid, prm.G * prm.GW * 32, plan->geo.smem_bytes, st>>>(prm);
+    fcc_fp32_kernel<KH, RS><<<grid, prm.G * prm.GW * 32, smem, st>>>(prm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fcc_fp32_kernel launch");
     return FCC_OK;
 }
 
 template <int KH>
-fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid)
+fcc_status_t launch_kh(const fcc_plan *plan, const Fp32Params &prm, cudaStream_t st, int grid, size_t smem)
 {
     const int rs = prm.Q <= 32 ? 1 : prm.Q / 32;
     switch (rs) {
-    case 1: return launch_inst<KH, 1>(plan, prm, st, grid);
-    case 2: return launch_inst<KH, 2>(plan, prm, st, grid);
-    case 4: return launch_inst<KH, 4>(plan, prm, st, grid);
-    case 8: return launch_inst<KH, 8>(plan, prm, st, grid);
+    case 1: return launch_inst<KH, 1>(plan, prm, st, grid, smem);
+    case 2: return launch_inst<KH, 2>(plan, prm, st, grid, smem);
+    case 4: return launch_inst<KH, 4>(plan, prm, st, grid, smem);
+    case 8: return launch_inst<KH, 8>(plan, prm, st, grid, smem);
     default: return fail(FCC_ERR_UNSUPPORTED, "the FP32 kernel needs N <= 1024");
     }
 }
@@ -241,6 +242,42 @@ Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long lo
     return prm;
 }
 
+// Tensor-core lag grid of the FP32 kernel (fcc_fp32_tiles.cuh): the weights of
+// lag steps m = 1 .. center, rounded up to a multiple of 32 rows, as three-term
+// FP16 split tables, scaled by a power of two that puts the largest |weight| in
+// [2^14, 2^15).  Built for folded plans with 6 or 8 bases per parity (the kernel
+// instances that carry the tensor-core code) and at least 32 lag steps each way;
+// FCC_FP32_MMA_RECON=0 leaves them out (the CUDA-core scan throughout).
+fcc_status_t prepare_fp32_mma(fcc_plan *plan)
+{
+    const fcc_plan_info_t &in = plan->info;
+    const char *env = getenv("FCC_FP32_MMA_RECON");
+    if (env && atoi(env) == 0) return FCC_OK;
+    if (in.form != FCC_FORM_FOLDED || plan->kh < 6 || in.center < 32) return FCC_OK;
+    const int npad = (in.center + 31) / 32 * 32;
+    if (npad > 256) return FCC_OK;
+    double wmax = 0.0;
+    for (int m = 1; m <= in.center; ++m) {
+        const int i = in.center + m;
+        const double ang = M_PI * 0.5 * (double)m / (double)in.den;
+        const double a = std::fabs(std::cos(ang)), b = std::fabs(std::sin(ang));
+        const double ab = 2.0 * std::max(a, b);
+        for (int k = 0; k < in.K_even; ++k) wmax = std::max(wmax, ab * std::fabs(plan->Ue[(size_t)i * in.K_even + k]));
+        for (int k = 0; k < in.K_odd; ++k) wmax = std::max(wmax, ab * std::fabs(plan->Uo[(size_t)i * in.K_odd + k]));
+    }
+    if (!(wmax > 0.0)) return FCC_OK;
+    int ex = 0;
+    std::frexp(wmax, &ex);  // wmax in [2^(ex-1), 2^ex)
+    const int shift = 15 - ex;
+    if (shift < -20 || shift > 20) return FCC_OK;
+    const std::vector<uint16_t> rt = recon_tables_f16(plan, npad, 1, shift, kMmaParts);
+    FCC_CUDA_TRY(dev_alloc(&plan->d_fp32_rbases, rt.size() * sizeof(uint16_t)));
+    FCC_CUDA_TRY(cudaMemcpy(plan->d_fp32_rbases, rt.data(), rt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    plan->fp32_npad = npad;
+    plan->fp32_rshift = shift;
+    return FCC_OK;
+}
+
 fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                          float *tau, float *coef, float *corr, cudaStream_t st)
 {
@@ -250,14 +287,28 @@ fcc_status_t launch_fp32(const fcc_plan *plan, const float2 *spectra, long long 
     if (n_tiles > 0x7fffffffLL) return fail(FCC_ERR_UNSUPPORTED, "too many frames for one call");
     if (plan->info.form == FCC_FORM_REIM_SPLIT && coef)
         return fail(FCC_ERR_UNSUPPORTED, "the split form has no coefficient output");
-    const Fp32Params prm = make_fp32_params(plan, spectra, T, idx, peak, tau, coef, corr, plan->d_err);
+    Fp32Params prm = make_fp32_params(plan, spectra, T, idx, peak, tau, coef, corr, plan->d_err);
     const int grid = (int)std::min<long long>(n_tiles, (long long)plan->num_sms);
     if (plan->info.form == FCC_FORM_REIM_SPLIT) return launch_fp32_reim(plan, prm, st, grid);
+    // the tensor-core lag grid wants one pair per lane (C = 4), groups of at most
+    // four warps (distinct tensor-memory row quadrants), every group's A (48),
+    // S and D columns inside 512 (64 + 2 npad each), and its tables and barriers
+    // behind the ring
+    size_t smem = g.smem_bytes;
+    const int npad = plan->fp32_npad;
+    const size_t extra = (size_t)kMmaHeader + (size_t)2 * kMmaParts * npad * 32;
+    if (plan->d_fp32_rbases && g.C == 4 && g.GW <= 4 && g.G * (64 + 2 * npad) <= 512 &&
+        g.smem_bytes + extra <= 232448) {
+        prm.rbases = plan->d_fp32_rbases;
+        prm.npad = npad;
+        prm.rshift = plan->fp32_rshift;
+        smem += extra;
+    }
     switch (plan->kh) {
-    case 2: return launch_kh<2>(plan, prm, st, grid);
-    case 4: return launch_kh<4>(plan, prm, st, grid);
-    case 6: return launch_kh<6>(plan, prm, st, grid);
-    case 8: return launch_kh<8>(plan, prm, st, grid);
+    case 2: return launch_kh<2>(plan, prm, st, grid, smem);
+    case 4: return launch_kh<4>(plan, prm, st, grid, smem);
+    case 6: return launch_kh<6>(plan, prm, st, grid, smem);
+    case 8: return launch_kh<8>(plan, prm, st, grid, smem);
     default: return fail(FCC_ERR_UNSUPPORTED, "more than 8 bases of one parity");
     }
 }

@@ -65,7 +65,26 @@ __device__ __forceinline__ int lone_off(int R, int B, int Q) { return R * B * 8 
 // accE holding v < KH and accO holding KH + v, and the reconstruction table
 // holds (2 U_c, 2 U_s) so that the same S -/+ D evaluation gives
 // y(+/-tau) = 2 (U_c c -/+ U_s s).
-template <int KH, int RS, bool FB>
+// Lag grid on the tensor cores (LG = single-plan launches; folded form, KH >= 6,
+// p.npad > 0, one pair per lane (C = 4) and groups of at most four warps).  Per
+// group the lanes write their coefficients into tensor memory as A rows (row =
+// 32 (warp % 4) + lane), each row scaled by a power of two that puts its largest
+// |z| in [2^14, 2^15) and split into three FP16 terms z1 + z2 + z3 (z minus the
+// three is below 2^-33 |z|max); one elected lane issues S = A_re W_S and D =
+// A_im W_D as six kind::f16 passes each (z1 w1, z2 w1, z1 w2, z1 w3, z2 w2,
+// z3 w1; what they leave out is below 2^-30 of a product) against the same
+// three-term split of the weights, resident in shared memory (lag steps m = 1 ..
+// npad, scaled by 2^rshift so that every |w| < 2^15), with FP32 accumulators.
+// The products are thus those of FP32 operands and better; the sums are FP32
+// sums, as in eval_SD.  The lanes read S and D back for the argmax (the same
+// outward scan and tie rule as the CUDA-core path), then evaluate y at the
+// chosen lag and its two neighbours with eval_SD, so that the peak and the
+// refinement are those of the CUDA-core path at that lag.  Rows whose
+// coefficients are zero, tiny or not finite take the CUDA-core scan.
+constexpr int kMmaHeader = 128;  // per group two barriers, then the tensor-memory slot
+constexpr int kMmaParts = 3;     // FP16 terms per coefficient and per weight
+
+template <int KH, int RS, bool FB, bool LG = false>
 __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *smem, long long tile_base,
                                            long long tile_stride, int n_local)
 {
@@ -78,6 +97,12 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
     float *basis = reinterpret_cast<float *>(smem + lay.basis_off);
     float *recon = reinterpret_cast<float *>(smem + lay.recon_off);
     unsigned char *stages = smem + lay.stage_off;
+    constexpr bool kMmaRecon = LG && !FB && KH >= 6;
+    const bool mma = kMmaRecon && p.npad > 0;
+    uint64_t *afull = reinterpret_cast<uint64_t *>(smem + lay.total);  // group: every A row written
+    uint64_t *dfull = afull + p.G;                                       // group: S and D complete
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + lay.total + 16 * p.G);
+    unsigned char *rtab = smem + lay.total + kMmaHeader;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int group = warp / p.GW, wig = warp - group * p.GW;
@@ -91,13 +116,37 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             mbar_init(&normd[s], (unsigned)p.GW);
             mbar_init(&freed[s], (unsigned)p.GW);
         }
+        if (mma)
+            for (int g = 0; g < p.G; ++g) {
+                mbar_init(&afull[g], (unsigned)p.GW);
+                mbar_init(&dfull[g], 1u);
+            }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int e = threadIdx.x; e < p.n_slots; e += blockDim.x) slots[e] = p.slots[e];
     for (int e = threadIdx.x; e < (p.Q + p.C + 1) * p.BS; e += blockDim.x) basis[e] = p.basis[e];
     for (int e = threadIdx.x; e < (p.center + 1) * 4 * KH; e += blockDim.x) recon[e] = p.recon[e];
+    uint32_t tmem = 0;
+    if (mma) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(p.rbases);
+        uint4 *dst = reinterpret_cast<uint4 *>(rtab);
+        for (int e = threadIdx.x; e < p.npad * 4 * kMmaParts; e += blockDim.x) dst[e] = src[e];  // 2 x 3 x npad x 32 B
+        __syncwarp();
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                         "r"(512u));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
     fence_proxy_async();
     __syncthreads();
+    if (mma) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = *tmem_slot;
+    }
+    unsigned rpar = 0;  // phase parity of this group's afull / dfull (one phase per tile)
+    int r_issued = 0;   // reconstruction commits issued by this group's leader
 
     auto tile_src = [&](int k, int &nf) {
         const long long tile = tile_base + (long long)k * tile_stride;
@@ -519,6 +568,164 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                 }
             }
         };
+        if (mma) {
+            // ---- 5'. the lag grid on the tensor cores (C = 4: one pair per lane)
+            __syncwarp();  // tcgen05.st / ld are warp-wide
+            const bool mine = active && pq >= 0;
+            const uint32_t lrow = (uint32_t)((warp & 3) * 32) << 16;  // this lane's tensor-memory row
+            const uint32_t gcol = tmem + (uint32_t)(group * (64 + 2 * p.npad));
+            float mx = 0.f, zs = 0.f;
+#pragma unroll
+            for (int v = 0; v < KH; ++v) {
+                float a0, a1, b0, b1;
+                upk(zE[v], a0, a1);
+                upk(zO[v], b0, b1);
+                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a0), fabsf(a1)), fmaxf(fabsf(b0), fabsf(b1))));
+                zs += (fabsf(a0) + fabsf(a1)) + (fabsf(b0) + fabsf(b1));
+            }
+            // a NaN fails the first test, an infinity or a tiny or zero row the others
+            const bool fine = mine && zs < 0x1p100f && mx >= 0x1p-90f;
+            const unsigned eb = (__float_as_uint(mx) >> 23) & 0xffu;        // mx in [2^(eb-127), 2^(eb-126))
+            const float zsc = fine ? __uint_as_float((268u - eb) << 23) : 0.f;  // 2^(141 - eb)
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {  // Re (S) then Im (D): z1, z2, z3, 8 columns each
+                uint32_t a[24];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float v[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int kk = 2 * j + e;
+                        float x = 0.f, y = 0.f;
+                        if (kk < 8) {
+                            if (kk < KH) upk(zE[kk], x, y);
+                        } else if (kk - 8 < KH) {
+                            upk(zO[kk - 8], x, y);
+                        }
+                        v[e] = (part ? y : x) * zsc;
+                    }
+                    // each difference is exact in FP32
+                    a[j] = f16x2(v[0], v[1]);
+                    const float r0 = v[0] - lo16(a[j]), r1 = v[1] - hi16(a[j]);
+                    a[8 + j] = f16x2(r0, r1);
+                    a[16 + j] = f16x2(r0 - lo16(a[8 + j]), r1 - hi16(a[8 + j]));
+                }
+                st8(lrow + gcol + 24 * part, a);
+                st8(lrow + gcol + 24 * part + 8, a + 8);
+                st8(lrow + gcol + 24 * part + 16, a + 16);
+                // tcgen05.st reads its registers asynchronously: a[] is not reused before the wait
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[group]);
+            if (leader) {
+                // every A row of the group written (so every lane has also read the
+                // previous tile's S and D)
+                if (mbar_wait(&afull[group], rpar, p.wait_cycles)) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // F32 accumulators, FP16 A and B, N = npad, M = 128
+                    const uint32_t idesc = (1u << 4) | ((uint32_t)(p.npad >> 3) << 17) | (8u << 24);
+                    const uint32_t rb = smem_u32(rtab), tb = (uint32_t)p.npad * 32;
+#pragma unroll
+                    for (int sd = 0; sd < 2; ++sd) {
+                        // S from the real parts (A columns 0..23), D from the imaginary ones (24..47)
+                        const uint32_t d = gcol + 64 + (uint32_t)(sd * p.npad), a0 = gcol + 24 * sd;
+                        const uint32_t w0 = rb + (uint32_t)(3 * sd) * tb;
+                        mma_f16_ta(d, a0, umma_desc(w0, 128, 256), idesc, false);            // z1 w1
+                        mma_f16_ta(d, a0 + 8, umma_desc(w0, 128, 256), idesc, true);         // z2 w1
+                        mma_f16_ta(d, a0, umma_desc(w0 + tb, 128, 256), idesc, true);        // z1 w2
+                        mma_f16_ta(d, a0, umma_desc(w0 + 2 * tb, 128, 256), idesc, true);    // z1 w3
+                        mma_f16_ta(d, a0 + 8, umma_desc(w0 + tb, 128, 256), idesc, true);    // z2 w2
+                        mma_f16_ta(d, a0 + 16, umma_desc(w0, 128, 256), idesc, true);        // z3 w1
+                    }
+                    umma_commit(&dfull[group]);
+                    ++r_issued;
+                } else {
+                    atomicOr(p.err, kErrTimeout);  // the group's dfull waits run out too
+                }
+            }
+            // lag step 0 in FP32 while the tensor cores run
+            float S0, D0;
+            eval_SD<KH>(recon, 0, zE, zO, S0, D0);
+            const float y0 = S0 - D0;
+            if (!__all_sync(FULLM, mbar_wait(&dfull[group], rpar, p.wait_cycles))) {
+                if (lane == 0) atomicOr(p.err, kErrTimeout);
+                break;
+            }
+            rpar ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float fs = zsc * __uint_as_float((uint32_t)(127 + p.rshift) << 23);  // the MMA values' scale
+            const float inv = fine ? __frcp_rn(fs) : 0.f;
+            const size_t o = mine ? (size_t)(f0 + fl) * p.P + pq : 0;
+            float *corr = (mine && p.out_corr) ? p.out_corr + o * p.I : nullptr;
+            // the outward scan of the CUDA-core path over the MMA values (scaled by fs)
+            float best = y0 * fs;
+            int bi = p.center;
+            auto take = [&](const float (&sv)[16], const float (&dv)[16], int c0) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int m = c0 + j + 1;
+                    if (m <= p.center) {
+                        const float ym = sv[j] + dv[j], yp = sv[j] - dv[j];  // y(center - m), y(center + m)
+                        if (ym >= best) {
+                            best = ym;
+                            bi = p.center - m;
+                        }
+                        if (yp > best) {
+                            best = yp;
+                            bi = p.center + m;
+                        }
+                        if (corr) {
+                            corr[p.center - m] = ym * inv;
+                            corr[p.center + m] = yp * inv;
+                        }
+                    }
+                }
+            };
+            const uint32_t tS = lrow + gcol + 64, tD = tS + (uint32_t)p.npad;
+            {
+                // two 16-column chunks in flight: the next one loads while this one is scanned
+                float sa[16], da[16], sb[16], db[16];
+                tmem_ld16_nw(tS, sa);
+                tmem_ld16_nw(tD, da);
+                tmem_wait_ld(sa, da);
+                for (int c0 = 0; c0 < p.npad; c0 += 32) {  // npad is a multiple of 32
+                    tmem_ld16_nw(tS + (uint32_t)(c0 + 16), sb);
+                    tmem_ld16_nw(tD + (uint32_t)(c0 + 16), db);
+                    take(sa, da, c0);
+                    __syncwarp();
+                    tmem_wait_ld(sb, db);
+                    if (c0 + 32 < p.npad) {
+                        tmem_ld16_nw(tS + (uint32_t)(c0 + 32), sa);
+                        tmem_ld16_nw(tD + (uint32_t)(c0 + 32), da);
+                    }
+                    take(sb, db, c0 + 16);
+                    __syncwarp();
+                    tmem_wait_ld(sa, da);
+                }
+            }
+            if (mine) {
+                if (fine) {
+                    // the chosen lag's value in FP32, as the CUDA-core scan computes it
+                    const int m = bi >= p.center ? bi - p.center : p.center - bi;
+                    float S, D;
+                    eval_SD<KH>(recon, m, zE, zO, S, D);
+                    best = bi >= p.center ? S - D : S + D;
+                    if (corr) {
+                        corr[p.center] = y0;
+                        corr[bi] = best;
+                    }
+                } else {
+                    best = y0;
+                    bi = p.center;
+                    if (corr) corr[p.center] = y0;
+                    scan(1, 1, best, bi, corr);
+                }
+                emit(o, bi, best);
+            }
+            continue;
+        }
         if (p.C == 4) {
             // one chunk lane per pair
             if (active && pq >= 0) {
@@ -574,6 +781,18 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
         for (int k = k_done + p.G; k < n_local && k <= k_done + p.S; k += p.G)
             if ((inflight >> (k % p.S)) & 1u)
                 if (!mbar_wait(&full[k % p.S], (unsigned)(k / p.S) & 1u, kWaitCycles)) atomicOr(p.err, kErrTimeout);
+    }
+    if (mma) {
+        // never free tensor memory under a reconstruction MMA still running
+        if (leader && r_issued > 0 && !mbar_wait(&dfull[group], (unsigned)(r_issued - 1) & 1u, kWaitCycles))
+            atomicOr(p.err, kErrTimeout);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp == 0) {
+            __syncwarp();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+        }
     }
 }
 

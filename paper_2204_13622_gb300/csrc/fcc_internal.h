@@ -112,6 +112,10 @@ struct Fp32Params {
     unsigned *err;
     long long wait_cycles;  // bound of every device-side wait (clock cycles)
     int inject;             // test hook: 1 = the copy of the plan's first tile is withheld
+    // lag grid on the tensor cores (single-plan folded launches; npad = 0: CUDA cores)
+    const void *rbases;     // FP16 [S 3 parts, D 3 parts][npad][16], lag steps m = 1 .. npad
+    int npad;               // a multiple of 32, >= center
+    int rshift;             // the weights are scaled by 2^rshift
 };
 
 // Batched FP32 form: one job = a run of consecutive tiles of one plan.
@@ -225,6 +229,8 @@ struct fcc_plan {
     void *d_tc_bases = nullptr;
     float *d_tc_peq = nullptr;
     void *d_tc_rbases = nullptr;       // reconstruction tables of the tensor-core path (or null)
+    void *d_fp32_rbases = nullptr;     // FP32 kernel: lag-grid tables for the tensor cores (or null)
+    int fp32_npad = 0, fp32_rshift = 0;
     int tc_npad = 0;
     int tc_F = 0;
     size_t tc_smem = 0;
@@ -244,6 +250,11 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan);
 // max_warps > 0 keeps only geometries of at most that many compute warps.
 fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out, int max_warps = 0);
 // Set the plan's FP32 geometry and rebuild its device tables for it.
+// FP16 hi / lo weight tables of the tensor-core lag-grid reconstruction (fcc_api.cu).
+std::vector<uint16_t> recon_tables_f16(const fcc_plan *plan, int npad, int m0, int shift, int parts);
+// FP32 kernel: builds the tensor-core lag-grid tables when the plan's grid is long
+// enough for them to pay (fcc_fp32.cu).
+fcc_status_t prepare_fp32_mma(fcc_plan *plan);
 fcc_status_t set_fp32_geometry(fcc_plan *plan, const Fp32Geometry &g);
 Fp32Params make_fp32_params(const fcc_plan *plan, const float2 *spectra, long long T, int *idx, float *peak,
                             float *tau, float *coef, float *corr, unsigned *err);

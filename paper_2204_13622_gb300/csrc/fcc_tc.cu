@@ -125,33 +125,6 @@ __device__ __forceinline__ float4 rec_f32(uint2 r)
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Two FP32 values rounded to one packed FP16 pair (element 0 in the low half).
-__device__ __forceinline__ uint32_t f16x2(float e0, float e1)
-{
-    uint32_t r;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(e1), "f"(e0));
-    return r;
-}
-__device__ __forceinline__ float lo16(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
-__device__ __forceinline__ float hi16(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
-
-// Eight 32-bit columns of this thread's tensor-memory lane.
-__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t *r)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-// D (tensor memory) += A (tensor memory, FP16) x B (shared-memory descriptor, FP16).
-__device__ __forceinline__ void mma_f16_ta(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, bool acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
-        "r"(a), "l"(bdesc), "r"(idesc), "r"((uint32_t)acc));
-}
-
 // Barriers (indices into the mbarrier array).
 enum {
     kFull = 0,     // raw tile landed (tx)
@@ -776,34 +749,7 @@ fcc_status_t prepare_tc(fcc_plan *plan)
     plan->tc_smem = L.total;
     plan->tc_npad = npad;
     if (npad) {
-        // [S hi, S lo, D hi, D lo][npad][16] FP16: row m holds the weights of lag step m
-        // on (Re zE[0..7], Re zO[0..7]) for S and on the imaginary parts for D
-        // (S = sum 2a Ue Re zE - 2b Uo Re zO, D = sum 2b Ue Im zE + 2a Uo Im zO at
-        // tau = m / den, a = cos(pi tau / 2), b = sin(pi tau / 2)); K-major core matrices
-        const int KE = in.K_even, KO = in.K_odd;
-        std::vector<uint16_t> rt((size_t)4 * npad * 16, 0);
-        auto put2 = [&](int t, int n, int k, double v) {
-            const __half h = __float2half_rn((float)v);
-            const __half l = __float2half_rn((float)(v - (double)__half2float(h)));
-            const size_t off = (((size_t)(n / 8) * 2 + k / 8) * 64 + (n % 8) * 8 + (k % 8));
-            rt[(size_t)(2 * t) * npad * 16 + off] = *reinterpret_cast<const uint16_t *>(&h);
-            rt[(size_t)(2 * t + 1) * npad * 16 + off] = *reinterpret_cast<const uint16_t *>(&l);
-        };
-        for (int m = 0; m <= in.center; ++m) {
-            const int i = in.center + m;
-            const double ang = M_PI * 0.5 * (double)m / (double)in.den;
-            const double a = std::cos(ang), b = std::sin(ang);
-            for (int k = 0; k < KE; ++k) {
-                const double u = plan->Ue[(size_t)i * KE + k];
-                put2(0, m, k, 2.0 * a * u);
-                put2(1, m, k, 2.0 * b * u);
-            }
-            for (int k = 0; k < KO; ++k) {
-                const double u = plan->Uo[(size_t)i * KO + k];
-                put2(0, m, 8 + k, -2.0 * b * u);
-                put2(1, m, 8 + k, 2.0 * a * u);
-            }
-        }
+        const std::vector<uint16_t> rt = recon_tables_f16(plan, npad, 0, 0, 2);
         FCC_CUDA_TRY(cudaMalloc(&plan->d_tc_rbases, rt.size() * sizeof(uint16_t)));
         FCC_CUDA_TRY(cudaMemcpy(plan->d_tc_rbases, rt.data(), rt.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     }

@@ -275,3 +275,69 @@ def test_circle8_full_size_sampled(B, O):
     plan.close()
     del X
     torch.cuda.empty_cache()
+
+
+# --------------------------------------------------------------------------
+# lag grid on the tensor cores (long grids, 6-8 bases per parity) against the
+# CUDA-core scan: the same argmax wherever the FP32 values' top two differ by
+# more than the FP32 tolerance, and there the same peak and refinement bit for
+# bit (both evaluate the chosen lag and its neighbours in FP32)
+# --------------------------------------------------------------------------
+def _with_ties(X, N, den, seed):
+    """Frames that stress the selection: a silent frame (every lag ties), a frame
+    whose microphones all carry one signal (zero lag wins, y symmetric), and
+    microphone m delayed by m h with h half-way between grid steps (pairs an odd
+    number of microphones apart sit between two lags: near-ties)."""
+    X = X.copy()
+    T, M = X.shape[:2]
+    rng = np.random.default_rng(seed)
+    f = np.arange(N // 2 + 1)
+    X[0] = 0
+    X[1] = X[1, :1]
+    for t in range(2, min(T, 40)):
+        S = rng.standard_normal(N // 2 + 1) + 1j * rng.standard_normal(N // 2 + 1)
+        h = (rng.integers(0, 6) + 0.5) / den
+        X[t] = np.stack([S * np.exp(-2j * np.pi * f * h * m / N) for m in range(M)])
+    return X.astype(np.complex64)
+
+
+@pytest.mark.parametrize("M,N,den,L,T", [
+    (16, 1024, 8, 12, 1500),
+    (16, 512, 4, 12, 700),
+    (13, 1024, 8, 12, 300),
+    (12, 1024, 8, 12, 300),
+])
+def test_tensor_core_lag_grid_against_cuda_core_scan(B, monkeypatch, M, N, den, L, T):
+    if (M, N) == (16, 1024):
+        X = workloads.GRID16.spectra(T=T, seed=5).numpy()
+    else:
+        X = _random_spectra(T, M, N, seed=M + T)
+    X = _with_ties(X, N, den, seed=M + T)
+    Xd = torch.from_numpy(X).cuda()
+    plan = B.Plan(M, 16000.0, N, den, tau_max=L)
+    monkeypatch.setenv("FCC_FP32_MMA_RECON", "0")
+    ref = B.Plan(M, 16000.0, N, den, tau_max=L)
+    monkeypatch.delenv("FCC_FP32_MMA_RECON")
+    b = ref.tdoa(Xd, corr=True)
+    ref.sync()
+    yb = b["corr"].cpu().numpy().astype(np.float64)
+    for corr in (False, True):
+        a = plan.tdoa(Xd, corr=corr)
+        plan.sync()
+        ia = a["lag_idx"].cpu().numpy()
+        check_argmax(ia, yb)
+        same = ia == b["lag_idx"].cpu().numpy()
+        assert same.mean() > 0.999
+        for key in ("peak", "tau_hat"):
+            assert np.array_equal(a[key].cpu().numpy()[same], b[key].cpu().numpy()[same]), key
+        if corr:
+            ca = a["corr"].cpu().numpy()
+            check_corr(ca, yb, rtol=1e-5)
+            # the kernel's peak is its own y at its argmax
+            own = np.take_along_axis(ca, ia[..., None].astype(np.int64), -1)[..., 0]
+            assert np.array_equal(a["peak"].cpu().numpy(), own)
+            if (M, N) == (16, 1024):
+                # the tensor-core values differ from the CUDA-core scan's in the last bits
+                assert not np.array_equal(ca, yb.astype(np.float32))
+    plan.close()
+    ref.close()
