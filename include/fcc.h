@@ -206,6 +206,10 @@ fcc_status_t fcc_plan_bases(const fcc_plan_t *plan, double *Pe, double *Po, doub
  *              Re z_e (K_even), Im z_e (K_even), Re z_o (K_odd), Im z_o (K_odd); or NULL
  *              (must be NULL for the split form: UNSUPPORTED).
  *   d_corr     device float [T][P][I]: the correlation y on the grid; or NULL.
+ *              FP32 plans with 6-8 bases of a parity and at least 32 lag steps
+ *              each way evaluate the grid on the tensor cores (a three-term
+ *              FP16 split, FP32 sums) and the argmax lag and its neighbours in
+ *              FP32; d_peak equals d_corr at d_lag_idx either way.
  *   stream     cudaStream_t or NULL.
  * Sizes the kernels take: FP32 plans N <= 1024, BF16 / FP16 plans
  * 128 <= N <= 1024, and at most 8 bases of each parity; other plans return
