@@ -247,6 +247,26 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, float (&v)[16])
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Four 32-bit columns of this thread's tensor-memory lane, without the wait.
+__device__ __forceinline__ void tmem_ld4_nw(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// tmem_wait_ld for two four-column loads.
+__device__ __forceinline__ void tmem_wait_ld4(float (&a)[4], float (&b)[4])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3])
+                 :
+                 : "memory");
+}
+
 // Waits for this thread's tcgen05.ld; the loaded arrays pass through the wait so
 // that no use of them is scheduled before it.
 __device__ __forceinline__ void tmem_wait_ld(float (&a)[16], float (&b)[16])

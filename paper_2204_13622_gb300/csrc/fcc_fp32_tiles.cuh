@@ -587,7 +587,7 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             const bool fine = mine && zs < 0x1p100f && mx >= 0x1p-90f;
             const unsigned eb = (__float_as_uint(mx) >> 23) & 0xffu;        // mx in [2^(eb-127), 2^(eb-126))
             const float zsc = fine ? __uint_as_float((268u - eb) << 23) : 0.f;  // 2^(141 - eb)
-#pragma unroll
+#pragma unroll 1
             for (int part = 0; part < 2; ++part) {  // Re (S) then Im (D): z1, z2, z3, 8 columns each
                 uint32_t a[24];
 #pragma unroll
@@ -659,15 +659,17 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
             const float inv = fine ? __frcp_rn(fs) : 0.f;
             const size_t o = mine ? (size_t)(f0 + fl) * p.P + pq : 0;
             float *corr = (mine && p.out_corr) ? p.out_corr + o * p.I : nullptr;
-            // the outward scan of the CUDA-core path over the MMA values (scaled by fs)
+            // the outward scan of the CUDA-core path over the MMA values (scaled by fs),
+            // four columns at a time with the next four loading; rolled, so that the
+            // epilogue stays small beside the record loop in the instruction cache
             float best = y0 * fs;
             int bi = p.center;
-            auto take = [&](const float (&sv)[16], const float (&dv)[16], int c0) {
+            auto take = [&](const float (&sv)[4], const float (&dv)[4], int c0) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 4; ++j) {
                     const int m = c0 + j + 1;
+                    const float ym = sv[j] + dv[j], yp = sv[j] - dv[j];  // y(center - m), y(center + m)
                     if (m <= p.center) {
-                        const float ym = sv[j] + dv[j], yp = sv[j] - dv[j];  // y(center - m), y(center + m)
                         if (ym >= best) {
                             best = ym;
                             bi = p.center - m;
@@ -676,33 +678,48 @@ __device__ __forceinline__ void fp32_tiles(const Fp32Params &p, unsigned char *s
                             best = yp;
                             bi = p.center + m;
                         }
-                        if (corr) {
-                            corr[p.center - m] = ym * inv;
-                            corr[p.center + m] = yp * inv;
-                        }
                     }
                 }
             };
             const uint32_t tS = lrow + gcol + 64, tD = tS + (uint32_t)p.npad;
             {
-                // two 16-column chunks in flight: the next one loads while this one is scanned
-                float sa[16], da[16], sb[16], db[16];
-                tmem_ld16_nw(tS, sa);
-                tmem_ld16_nw(tD, da);
-                tmem_wait_ld(sa, da);
-                for (int c0 = 0; c0 < p.npad; c0 += 32) {  // npad is a multiple of 32
-                    tmem_ld16_nw(tS + (uint32_t)(c0 + 16), sb);
-                    tmem_ld16_nw(tD + (uint32_t)(c0 + 16), db);
+                float sa[4], da[4], sb[4], db[4];
+                tmem_ld4_nw(tS, sa);
+                tmem_ld4_nw(tD, da);
+                tmem_wait_ld4(sa, da);
+#pragma unroll 1
+                for (int c0 = 0; c0 < p.npad; c0 += 8) {  // npad is a multiple of 32
+                    tmem_ld4_nw(tS + (uint32_t)(c0 + 4), sb);
+                    tmem_ld4_nw(tD + (uint32_t)(c0 + 4), db);
                     take(sa, da, c0);
                     __syncwarp();
-                    tmem_wait_ld(sb, db);
-                    if (c0 + 32 < p.npad) {
-                        tmem_ld16_nw(tS + (uint32_t)(c0 + 32), sa);
-                        tmem_ld16_nw(tD + (uint32_t)(c0 + 32), da);
+                    tmem_wait_ld4(sb, db);
+                    if (c0 + 8 < p.npad) {
+                        tmem_ld4_nw(tS + (uint32_t)(c0 + 8), sa);
+                        tmem_ld4_nw(tD + (uint32_t)(c0 + 8), da);
                     }
-                    take(sb, db, c0 + 16);
+                    take(sb, db, c0 + 4);
                     __syncwarp();
-                    tmem_wait_ld(sa, da);
+                    tmem_wait_ld4(sa, da);
+                }
+            }
+            if (p.out_corr) {
+                // the correlation output (tests, diagnostics): every lag from the MMA values
+#pragma unroll 1
+                for (int c0 = 0; c0 < p.npad; c0 += 16) {
+                    float sv[16], dv[16];
+                    __syncwarp();
+                    tmem_ld16_nw(tS + (uint32_t)c0, sv);
+                    tmem_ld16_nw(tD + (uint32_t)c0, dv);
+                    tmem_wait_ld(sv, dv);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int m = c0 + jj + 1;
+                        if (corr && m <= p.center) {
+                            corr[p.center - m] = (sv[jj] + dv[jj]) * inv;
+                            corr[p.center + m] = (sv[jj] - dv[jj]) * inv;
+                        }
+                    }
                 }
             }
             if (mine) {
