@@ -72,9 +72,11 @@ __device__ __forceinline__ int lone_off(int R, int B, int Q) { return R * B * 8 
 // |z| in [2^14, 2^15) and split into three FP16 terms z1 + z2 + z3 (z minus the
 // three is below 2^-33 |z|max); one elected lane issues S = A_re W_S and D =
 // A_im W_D as six kind::f16 passes each (z1 w1, z2 w1, z1 w2, z1 w3, z2 w2,
-// z3 w1; what they leave out is below 2^-30 of a product) against the same
-// three-term split of the weights, resident in shared memory (lag steps m = 1 ..
-// npad, scaled by 2^rshift so that every |w| < 2^15), with FP32 accumulators.
+// z3 w1) against the same three-term split of the weights, resident in shared
+// memory (lag steps m = 1 .. npad, scaled by 2^rshift so that every |w| <
+// 2^15), with FP32 accumulators.  What the six leave out is below 2^-30 of
+// sum_k |z_k w_k|, plus at most 2^-25 per FP16 subnormal term (below 2^-38 of
+// the largest |z| or |w|).
 // The products are thus those of FP32 operands and better; the sums are FP32
 // sums, as in eval_SD.  The lanes read S and D back for the argmax (the same
 // outward scan and tie rule as the CUDA-core path), then evaluate y at the
