@@ -250,7 +250,7 @@ fcc_status_t choose_fp32_geometry(fcc_plan *plan);
 // max_warps > 0 keeps only geometries of at most that many compute warps.
 fcc_status_t fp32_candidates(const fcc_plan *plan, std::vector<Fp32Geometry> &out, int max_warps = 0);
 // Set the plan's FP32 geometry and rebuild its device tables for it.
-// FP16 hi / lo weight tables of the tensor-core lag-grid reconstruction (fcc_api.cu).
+// FP16 split weight tables (`parts` terms) of the tensor-core lag grids (fcc_api.cu).
 std::vector<uint16_t> recon_tables_f16(const fcc_plan *plan, int npad, int m0, int shift, int parts);
 // FP32 kernel: builds the tensor-core lag-grid tables when the plan's grid is long
 // enough for them to pay (fcc_fp32.cu).
